@@ -1,0 +1,39 @@
+"""Input recipes: determinism, mask volume, flip count (CPU only)."""
+
+import math
+
+import numpy as np
+
+from paper_1907_07774_gb300 import synth
+
+
+def test_tissue_maps_are_seeded_partition_of_unity_inside_mask():
+    a = synth.tissue_maps((16, 16, 16), 3)
+    b = synth.tissue_maps((16, 16, 16), 3)
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+    mask = synth.ellipsoid_mask((16, 16, 16))
+    tot = a[0] + a[1] + a[2]
+    assert np.allclose(tot[mask > 0], 1.0) and np.all(tot[mask == 0] == 0)
+
+
+def test_mask_volume_close_to_ellipsoid_fraction():
+    mask = synth.ellipsoid_mask((64, 64, 64))
+    want = 4.0 / 3.0 * math.pi * 0.8 * 0.9 * 0.7 * math.pi ** 3 / (2 * math.pi) ** 3
+    assert abs(mask.mean() - want) < 0.01
+
+
+def test_labels_flip_exact_count_inside_mask():
+    n = (16, 16, 16)
+    mask = synth.ellipsoid_mask(n)
+    c = np.zeros(n)
+    d = synth.labels(c, mask, 1, flip_fraction=0.05)
+    assert d.sum() == round(0.05 * mask.sum())
+    assert np.all(d[mask == 0] == 0)
+
+
+def test_lattice_centred_and_spaced():
+    c = synth.lattice_centers(3, 0.5)
+    assert c.shape == (27, 3)
+    assert np.allclose(c.mean(axis=0), math.pi)
+    assert np.allclose(np.unique(c[:, 2]) - math.pi, [-0.5, 0.0, 0.5])
