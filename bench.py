@@ -1,0 +1,371 @@
+#!/usr/bin/env python
+"""Benchmark: forward + adjoint reduced gradient of the tumor
+reaction-diffusion model at 256^3 (nt = 32, 125 Gaussians), in cell-updates/s.
+
+One step = one ``rd_gradient`` call: Gaussian synthesis, the Strang/CN
+forward solve with PCG, the misfit, the discrete adjoint sweep and the
+gradient assembly (p, k_f, rho_f).  cell-updates/s = n^3 * nt / step time.
+
+Inputs are seeded synthetic brain-like fields (``synth.calibration_problem``)
+resident in HBM before the timed region for ``value``; ``e2e`` repeats the
+step through the C ABI from pinned host buffers (tissue maps and data copied
+in, gradient copied out, every step).  Every field is 64 MiB (FP32) or more,
+so the working set (> 2 GiB) is far larger than L2.
+
+``--impl reference`` times the FP64 CPU oracle on the host instead (a
+bounded sample: one operator application and one preconditioner
+application at the same grid, scaled by the PCG work of the gradient).
+Multi-GPU runs (torchrun) execute independent replicas, one per rank.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fwd+adjoint gradient cell-updates/s at 256^3 (FP32-mixed vs FP64, same GB300), %HBM peak"
+UNIT = "cell-updates/s"
+FALLBACK_HBM_GBS = 6800.0
+# PCG work of one FP64 gradient of this workload (rtol 1e-10), measured on
+# the GPU FP64 path; used to scale the CPU oracle sample in the reference arm.
+FP64_WORK = {"iters": 1611, "solves": 64}
+
+
+def env_rank():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
+        int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def problem(n, nt):
+    from paper_1907_07774_gb300 import synth
+    return synth.calibration_problem(n=n, nt=nt, m=5)
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            d = json.load(open(path))
+            for k in ("hbm_gbs", "hbm_GBs", "hbm"):
+                if k in d:
+                    return float(d[k]), "measured"
+        except Exception:
+            pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def csrc_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_1907_07774_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(cls, n):
+    """Per-launch DRAM bytes of a kernel class from the committed ncu
+    summary, if it was taken on the current kernel sources."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        d = json.load(open(path))
+    except Exception:
+        return None
+    if d.get("csrc_hash") != csrc_hash():
+        return None
+    ent = d.get("classes", {}).get(cls)
+    if not ent:
+        return None
+    return float(ent["bytes_per_launch"]) * (n ** 3) / float(ent.get("cells", n ** 3))
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except Exception:
+                self.p.kill()
+
+    def summary(self):
+        self.f.flush()
+        rows = []
+        try:
+            for line in open(self.f.name):
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9 and parts[1].replace(".", "").isdigit():
+                    rows.append(parts)
+        except Exception:
+            pass
+        finally:
+            try:
+                os.unlink(self.f.name)
+            except Exception:
+                pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for name, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": float(rows[0][2]),
+                "reasons": sorted(reasons), "samples": len(rows),
+                "power_w_median": statistics.median(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())
+                if any(r[3].replace(".", "").isdigit() for r in rows) else None}
+
+
+# algorithmic fields moved per launch of each kernel class
+FIELDS_PER_LAUNCH = {"op_axis01": 4, "op_axis2": 3, "pcg_opx": 5, "dht_plain": 2, "dht_sym": 2,
+                     "dht_setup": 2, "dht_update": 7, "grad": 4}
+
+
+def cpu_oracle_sample(n, nt, k_f, seconds_budget=30.0):
+    """Time one FP64 oracle operator application and one preconditioner
+    application on the host at grid n (the work of one PCG iteration)."""
+    import numpy as np
+    from oracle import rd as orc
+    prob = problem(n, nt)
+    M = orc.model_from_problem(prob, kind="numpy")
+    u = np.random.default_rng(0).standard_normal(prob.n)
+    t0 = time.perf_counter()
+    M.A(u, k_f)
+    t1 = time.perf_counter()
+    M.sp.precond(u, M.s * k_f * float(np.mean(M.kappa1)))
+    t2 = time.perf_counter()
+    return t1 - t0, t2 - t1
+
+
+def cpu_cells_per_s(n, nt, t_apply, t_prec, iters, solves):
+    # per PCG iteration: one operator + one preconditioner; per solve: one
+    # right-hand-side operator and one preconditioner; per adjoint step: the
+    # k_f integrand (six transforms, ~3/4 of an operator)
+    t = iters * (t_apply + t_prec) + solves * (t_apply + t_prec) + nt * 0.75 * t_apply
+    return n ** 3 * nt / t, t
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    n, nt = args.n, args.nt
+    vals = []
+    last = None
+    for i in range(args.warmup + args.steps):
+        ta, tp = cpu_oracle_sample(n, nt, 0.02)
+        v, tgrad = cpu_cells_per_s(n, nt, ta, tp, FP64_WORK["iters"], FP64_WORK["solves"])
+        if i >= args.warmup:
+            vals.append(v)
+            last = (ta, tp, tgrad)
+    value = statistics.median(vals)
+    sample = (f"oracle (numpy FFT, FP64) one operator application ({last[0]:.2f} s) and one "
+              f"preconditioner application ({last[1]:.2f} s) at {n}^3, scaled by the PCG work of "
+              f"the FP64 gradient ({FP64_WORK['iters']} iterations, {FP64_WORK['solves']} solves, nt={nt}): "
+              f"{last[2]:.0f} s per gradient")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * n ** 3 * nt / value,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": f"rd_gradient {n}^3 nt={nt} np=125 fp64 oracle"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args, rank, world, local):
+    import numpy as np
+    import torch
+
+    from paper_1907_07774_gb300 import build as _build
+    from paper_1907_07774_gb300 import rd as R
+    from paper_1907_07774_gb300 import synth
+
+    _build.build()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    n, nt = args.n, args.nt
+    prob = problem(n, nt)
+    ctx = R.context_for(prob, prec="mixed", pcg_rtol=1e-6, pcg_maxit=500, ckpt_stride=args.ckpt_stride)
+    c_true = torch.zeros(prob.n, dtype=torch.float64, device="cuda")
+    ctx.rd_forward(prob.p_true, prob.k_f_true, prob.rho_f_true, c_true)
+    d_host = synth.labels(c_true.cpu().numpy(), synth.ellipsoid_mask(prob.n), prob.seed + 7)
+    d_dev = torch.from_numpy(d_host).cuda()
+    m_dev = [torch.from_numpy(x).cuda() for x in (prob.m_wm, prob.m_gm, prob.m_csf)]
+    ctx.rd_set_tissue(*m_dev)
+    ctx.rd_set_data(d_dev)
+    p, k_f, rho_f = prob.p, prob.k_f, prob.rho_f
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        J, g = ctx.rd_gradient(p, k_f, rho_f)
+    iters, solves = ctx.rd_last_pcg_iters(), ctx.rd_last_pcg_solves()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---- device-resident timed region (with live per-launch event timing)
+    R.rd_profile_enable(True)
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            J, g = ctx.rd_gradient(p, k_f, rho_f)
+        e1.record(stream)
+        barrier()
+    prof = R.rd_profile_read()
+    R.rd_profile_enable(False)
+    ms = e0.elapsed_time(e1)
+    clocks = clk.summary()
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    cells = n ** 3 * nt
+    value = world * cells * args.steps / (ms / 1e3)
+    launches = int(sum(c for _, c in prof.values()))
+
+    # ---- roofline of the dominant kernel class
+    esz = 4
+    dom = max((k for k in prof if k in FIELDS_PER_LAUNCH), key=lambda k: prof[k][0])
+    dms, dcount = prof[dom]
+    alg_bytes = FIELDS_PER_LAUNCH[dom] * n ** 3 * esz
+    achieved = alg_bytes / (dms / dcount / 1e3) / 1e9
+    peak, peak_kind = measured_peaks()
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": peak_kind,
+                "traffic": ncu_traffic(dom, n), "alg_bytes_per_launch": alg_bytes,
+                "avg_launch_us": 1e3 * dms / dcount, "launches": dcount,
+                "share_of_step": dms / ms}
+    per_class = {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps}
+                 for k, v in prof.items() if v[1]}
+
+    # ---- end to end through the C ABI from pinned host buffers
+    host_m = [torch.from_numpy(x).pin_memory() for x in (prob.m_wm, prob.m_gm, prob.m_csf)]
+    host_d = torch.from_numpy(d_host).pin_memory()
+    barrier()
+    e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2.record(stream)
+    for _ in range(args.steps):
+        ctx.rd_set_tissue(*host_m)
+        ctx.rd_set_data(host_d)
+        Je, ge = ctx.rd_gradient(p, k_f, rho_f)
+    e3.record(stream)
+    barrier()
+    ms_e2e = e2.elapsed_time(e3)
+    if dist is not None:
+        t = torch.tensor([ms_e2e], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_e2e = float(t.item())
+    e2e = {"value": world * cells * args.steps / (ms_e2e / 1e3), "unit": UNIT,
+           "h2d_bytes_per_step": 4 * n ** 3 * 8 + len(p) * 8,
+           "d2h_bytes_per_step": (len(p) + 2) * 8 + 8}
+
+    # ---- FP64 path on the same GPU
+    fp64 = None
+    if args.fp64_steps > 0 and rank == 0:
+        del ctx
+        torch.cuda.empty_cache()
+        c64 = R.context_for(prob, prec="fp64", pcg_rtol=1e-10, pcg_maxit=1000, ckpt_stride=args.ckpt_stride)
+        c64.rd_set_data(d_dev)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.fp64_steps):
+            J64, g64 = c64.rd_gradient(p, k_f, rho_f)
+        torch.cuda.synchronize()
+        s64 = (time.perf_counter() - t0) / args.fp64_steps
+        fp64 = {"value": cells / s64, "ms_per_step": 1e3 * s64, "pcg_iters": c64.rd_last_pcg_iters(),
+                "pcg_solves": c64.rd_last_pcg_solves(),
+                "mixed_speedup": (cells * args.steps / (ms / 1e3)) / (cells / s64),
+                "mixed_grad_rel_err_vs_fp64": float(np.linalg.norm(g - g64) / np.linalg.norm(g64)),
+                "mixed_misfit_rel_err_vs_fp64": abs(J - J64) / abs(J64)}
+        del c64
+
+    # ---- CPU oracle baseline (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        w = fp64 or {"pcg_iters": FP64_WORK["iters"], "pcg_solves": FP64_WORK["solves"]}
+        ta, tp = cpu_oracle_sample(n, nt, k_f)
+        v, tgrad = cpu_cells_per_s(n, nt, ta, tp, w["pcg_iters"], w["pcg_solves"])
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"one FP64 operator application ({ta:.2f} s) and one preconditioner application "
+                         f"({tp:.2f} s) of the oracle (numpy FFT) at {n}^3, scaled by the FP64 gradient's "
+                         f"PCG work ({w['pcg_iters']} iterations, {w['pcg_solves']} solves): {tgrad:.0f} s"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": f"rd_gradient {n}^3 nt={nt} np={len(p)} mixed (FP32 fields, FP64 "
+                                       f"reductions) pcg_rtol=1e-6", "grid": n, "nt": nt, "np": len(p),
+                           "ckpt_stride": args.ckpt_stride, "l2": "inputs larger than L2 (fields 64 MiB, "
+                                                                 "working set > 2 GiB)",
+                           "parallelism": "replicas" if world > 1 else "single"},
+                "misfit": J, "pcg_iters_per_step": iters, "pcg_solves_per_step": solves,
+                "gpu_launches": launches, "clocks": clocks, "roofline": roofline, "e2e": e2e,
+                "cpu_baseline": cpu, "fp64": fp64, "kernel_classes": per_class}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--nt", type=int, default=32)
+    ap.add_argument("--ckpt-stride", type=int, default=0)
+    ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank, world, local = env_rank()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    return run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,166 @@
+/*
+ * librd: forward / adjoint / gradient / Gauss-Newton Hessian-vector solve of
+ * the tumor reaction-diffusion model
+ *
+ *     dc/dt = div(kappa(x) grad c) + rho(x) c (1 - c)      in [0, 2 pi)^3 x (0, 1]
+ *     c(0)  = Phi p = sum_i p_i exp(-|x - x_i|^2 / (2 sigma^2))
+ *     kappa = k_f sum_i k_i m_i,   rho = rho_f sum_i rho_i m_i
+ *
+ * (Scheufele et al., "Image-driven biophysical tumor growth model
+ * calibration": state equation Eq. tumor:fwd and tumor:fwd-init, coefficients
+ * Eq. coeff_tumor, adjoint Eq. tumor:adj / tumor:adj-final, gradients Eq.
+ * tumor:inv and tumor:inv_diff, discretisation Sec. 3.3: Fourier
+ * pseudo-spectral derivatives on a periodic grid, second-order Strang
+ * splitting with the exact logistic reaction step and Crank-Nicolson
+ * diffusion).  The Crank-Nicolson system (I - tau/2 A) x = b is solved by
+ * preconditioned CG with the spectral constant-coefficient preconditioner
+ * 1 / (1 + tau/2 * mean(kappa) * |k|^2).
+ *
+ * Plain C ABI: host or device pointers and sizes only.  One context drives
+ * one grid on the current CUDA device and one stream.
+ *
+ * Conventions
+ *   - Grid n[0] x n[1] x n[2], n[2] fastest (C order); point i of an axis of
+ *     length n sits at x = 2 pi i / n.  Each n[a] must be one of
+ *     8, 16, 32, 64, 128, 256 (RD_ERR_SHAPE otherwise).
+ *   - Every field passed in or out is FP64 and may live in host or device
+ *     memory (unified addressing decides); it is only read (or written)
+ *     during the call, the library keeps its own copy.
+ *   - Parameter vectors (p, v, gradients) are FP64 host arrays of length
+ *     np + 2 laid out [p_1 .. p_np, k_f, rho_f] where a full vector is meant.
+ *   - Misfit J = 1/2 h^3 sum_x (c(1) - d)^2 + 1/2 beta_p |p|^2 with
+ *     h^3 = (2 pi)^3 / (n0 n1 n2) (the L2 quadrature of D_c, Table 1).
+ *   - Adjoint convention: alpha(1) = d - c(1) (Eq. tumor:adj-final).
+ *   - Errors are returned as status codes; a call never aborts the process.
+ *     rd_last_error() gives a message.  RD_ERR_NOCONV means some PCG solve
+ *     hit pcg_maxit; results are still written.
+ *   - A context is not thread safe.  Calls are ordered on its stream; calls
+ *     returning host values (rd_gradient, rd_hessvec, rd_forward with a
+ *     misfit) synchronise that stream.
+ */
+#ifndef RD_H
+#define RD_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rd_ctx rd_ctx;
+
+typedef enum {
+  RD_OK = 0,
+  RD_ERR_ARG = 1,        /* null pointer or out-of-range argument           */
+  RD_ERR_SHAPE = 2,      /* unsupported grid size                           */
+  RD_ERR_CUDA = 3,       /* a CUDA call failed (message in rd_last_error)   */
+  RD_ERR_NOMEM = 4,      /* workspace too small / allocation failed         */
+  RD_ERR_NOCONV = 5,     /* a PCG solve reached pcg_maxit                   */
+  RD_ERR_NONFINITE = 6,  /* a NaN or Inf appeared in a reduction            */
+  RD_ERR_STATE = 7       /* a required rd_set_* call has not been made      */
+} rd_status;
+
+typedef enum { RD_FP64 = 0, RD_MIXED = 1 } rd_precision;
+
+typedef struct {
+  int n[3];          /* grid                                                 */
+  int nt;            /* time steps to t_end                                  */
+  double t_end;      /* final time (1.0 in the normalised model)             */
+  int prec;          /* RD_FP64: all FP64.  RD_MIXED: fields in FP32,
+                        reductions, norms and scalars in FP64               */
+  double pcg_rtol;   /* stop when ||r|| <= pcg_rtol ||f|| (f: rhs of the
+                        increment system (I - tau/2 A) dx = f, dx0 = 0)      */
+  int pcg_maxit;
+  int ckpt_stride;   /* 0: keep every step's state for the adjoint;
+                        s > 0: keep every s-th state and recompute segments  */
+  double k_w[3];     /* k_i of Eq. coeff_tumor (WM, GM, CSF)                */
+  double rho_w[3];   /* rho_i of Eq. coeff_tumor                            */
+  double beta_p;     /* weight of 1/2 |p|^2 in the objective                 */
+} rd_config;
+
+/* Fill *cfg with defaults: 64^3, nt 16, t_end 1, FP64, rtol 1e-10, maxit
+ * 200, store all steps, k = (1, 0.1, 0), rho = (1, 0.2, 0), beta_p 0. */
+rd_status rd_config_default(rd_config* cfg);
+
+/* Device workspace in bytes that rd_create needs for cfg and np Gaussians. */
+rd_status rd_workspace_size(const rd_config* cfg, int np, size_t* bytes);
+
+/* Create a context.  workspace: device memory of at least
+ * rd_workspace_size() bytes, 256-byte aligned, owned by the caller and kept
+ * alive until rd_destroy; NULL makes the library allocate (and free) it.
+ * stream: a cudaStream_t (NULL = legacy default stream). */
+rd_status rd_create(rd_ctx** out, const rd_config* cfg, int np, void* workspace,
+                    size_t workspace_bytes, void* stream);
+
+/* Tissue probability maps m_WM, m_GM, m_CSF (Sec. 2 notation), FP64, each
+ * n0 n1 n2 values; kappa1 = sum k_i m_i and rho1 = sum rho_i m_i are formed
+ * on the device (Eq. coeff_tumor). */
+rd_status rd_set_tissue(rd_ctx* ctx, const double* m_wm, const double* m_gm, const double* m_csf);
+
+/* Gaussian basis (Eq. tumor:fwd-init): centers is a host array [np][3] in
+ * box coordinates, sigma the common width.  Minimum-image distance. */
+rd_status rd_set_basis(rd_ctx* ctx, const double* centers, double sigma);
+
+/* Target data d (FP64 field) for the misfit. */
+rd_status rd_set_data(rd_ctx* ctx, const double* d);
+
+/* State solve (Eq. tumor:fwd): c(1) for parameters (p, k_f, rho_f); p is a
+ * host array of np values.  c1_out (FP64 field, may be NULL) receives c(1);
+ * misfit (host, may be NULL) receives J if data are set. */
+rd_status rd_forward(rd_ctx* ctx, const double* p, double k_f, double rho_f, double* c1_out,
+                     double* misfit);
+
+/* Adjoint solve (Eq. tumor:adj) for the last rd_forward: alpha(0) into
+ * alpha0_out (FP64 field, may be NULL); the reduced gradient of that point
+ * is kept and can be read with rd_last_gradient. */
+rd_status rd_adjoint(rd_ctx* ctx, double* alpha0_out);
+
+/* Misfit and reduced gradient [g_p (np), g_kf, g_rhof] (Eq. tumor:inv,
+ * tumor:inv_diff and the rho_f analogue) at (p, k_f, rho_f).  grad is a
+ * host array of np + 2 values.  Synchronises. */
+rd_status rd_gradient(rd_ctx* ctx, const double* p, double k_f, double rho_f, double* misfit,
+                      double* grad);
+
+/* Gradient of the last rd_adjoint / rd_gradient call (host, np + 2). */
+rd_status rd_last_gradient(const rd_ctx* ctx, double* grad);
+
+/* Gauss-Newton Hessian-vector product H v = J^T (h^3 J v) + beta_p v_p with
+ * J = d c(1) / d(p, k_f, rho_f), from the tangent-linear model and the
+ * adjoint of the same discretisation.  v and Hv: host, np + 2.
+ * Synchronises. */
+rd_status rd_hessvec(rd_ctx* ctx, const double* p, double k_f, double rho_f, const double* v,
+                     double* Hv);
+
+/* Building blocks, exposed for testing and for callers composing their own
+ * solvers.  Au = k_f div(kappa1 grad u) with the Fourier pseudo-spectral
+ * derivatives of Sec. 3.3 (i k zeroed at the Nyquist index); z = M^-1 r with
+ * M^-1 = F^-1 diag(1 / (1 + tau/2 k_f mean(kappa1) |k|^2)) F, the PCG
+ * preconditioner.  Fields FP64, host or device; needs rd_set_tissue. */
+rd_status rd_apply_operator(rd_ctx* ctx, double k_f, const double* u, double* Au);
+rd_status rd_apply_precond(rd_ctx* ctx, double k_f, const double* r, double* z);
+
+/* Counters of the last call: PCG iterations summed over its solves, and
+ * the number of solves. */
+int rd_last_pcg_iters(const rd_ctx* ctx);
+int rd_last_pcg_solves(const rd_ctx* ctx);
+
+/* Optional launch timing, process wide.  rd_profile_enable(1) clears the
+ * totals and brackets every kernel launch with two CUDA events on its stream;
+ * rd_profile_read waits for the recorded events and fills, per kernel class
+ * (names from rd_profile_class), the summed device milliseconds and the
+ * launch counts; it returns the number of classes. */
+void rd_profile_enable(int on);
+int rd_profile_read(double* ms, long long* launches, int n);
+const char* rd_profile_class(int i);
+
+/* Message of the last failing call ("" if none). */
+const char* rd_last_error(const rd_ctx* ctx);
+
+/* Release the context (and the workspace if the library allocated it). */
+void rd_destroy(rd_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RD_H */

@@ -1,0 +1,1059 @@
+// Host orchestration of the reaction-diffusion solve and the C ABI of
+// include/rd.h.
+//
+// One time step (Sec. 3.3, Strang splitting, read as L(tau/2) CN(tau)
+// L(tau/2)):
+//   c*  = L_s(c_n)                      s = tau/2, exact logistic flow
+//   c** = c* + dx,  (I - s A) dx = 2 s A c*      (Crank-Nicolson increment)
+//   c_{n+1} = L_s(c**)
+// The adjoint sweep is the exact transpose of this step (the CN matrix is
+// symmetric; the logistic step transposes to multiplication by dL_s/dc),
+// with alpha(1) = d - c(1) (Eq. tumor:adj-final) and the parameter
+// gradients of Eq. tumor:inv / tumor:inv_diff accumulated on the way back.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/rd.h"
+#include "rd_launch.cuh"
+
+namespace rd {
+
+bool supported_length(int L) {
+  return L == 8 || L == 16 || L == 32 || L == 64 || L == 128 || L == 256;
+}
+
+// ------------------------------------------------------- launch timing
+namespace {
+struct Profiler {
+  std::mutex mu;
+  bool on = false;
+  std::vector<cudaEvent_t> pool;
+  struct Rec { int cls; cudaEvent_t a, b; };
+  std::vector<Rec> pending;
+  double ms[kcCount] = {};
+  long long count[kcCount] = {};
+  cudaEvent_t get() {
+    if (!pool.empty()) {
+      cudaEvent_t e = pool.back();
+      pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+  }
+  void drain() {
+    for (auto& r : pending) {
+      float t = 0.f;
+      if (cudaEventSynchronize(r.b) == cudaSuccess && cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) {
+        ms[r.cls] += t;
+        count[r.cls] += 1;
+      }
+      pool.push_back(r.a);
+      pool.push_back(r.b);
+    }
+    pending.clear();
+  }
+};
+Profiler& prof() {
+  static Profiler p;
+  return p;
+}
+const char* kClassNames[kcCount] = {"op_axis2",   "op_axis01",  "pcg_opx", "dht_setup", "dht_plain",
+                                    "dht_update", "dht_sym",    "grad",    "pointwise", "other"};
+}  // namespace
+
+int prof_begin(int cls, cudaStream_t s) {
+  Profiler& p = prof();
+  if (!p.on) return -1;
+  std::lock_guard<std::mutex> lk(p.mu);
+  Profiler::Rec r{cls, p.get(), p.get()};
+  cudaEventRecord(r.a, s);
+  p.pending.push_back(r);
+  return (int)p.pending.size() - 1;
+}
+
+void prof_end(int token, cudaStream_t s) {
+  if (token < 0) return;
+  Profiler& p = prof();
+  std::lock_guard<std::mutex> lk(p.mu);
+  if (token < (int)p.pending.size()) cudaEventRecord(p.pending[token].b, s);
+}
+
+namespace {
+
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+constexpr int kNumL = 6;   // 8 .. 256
+inline int lidx(int L) {
+  int i = 0;
+  while ((8 << i) < L) ++i;
+  return i;
+}
+
+// Bump allocator over the caller's workspace (256-byte alignment).
+struct Carve {
+  char* base;
+  size_t off = 0, cap;
+  bool measure;
+  void* take(size_t bytes) {
+    off = (off + 255) & ~size_t(255);
+    void* p = measure ? nullptr : base + off;
+    off += bytes;
+    return p;
+  }
+};
+
+inline bool is_device_ptr(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+enum Field {
+  F_KAPPA1, F_RHO1, F_C0, F_D, F_ALPHA, F_AB, F_WS, F_CN, F_CS,
+  F_X, F_R, F_P, F_Q, F_W1, F_W2, F_CH, F_CHS, F_U, F_COUNT
+};
+
+}  // namespace
+
+struct EngineBase {
+  virtual ~EngineBase() {}
+  rd_config cfg{};
+  int np = 0;
+  Geom g{};
+  long long nn = 0;
+  cudaStream_t stream = nullptr;
+  char err[512] = {0};
+  int last_iters = 0, last_solves = 0;
+  bool have_tissue = false, have_basis = false, have_data = false;
+  bool have_traj = false, have_grad = false;
+  double theta_kf = 0, theta_rho = 0;
+  std::vector<double> theta_p, last_grad;
+  bool nonconv = false;
+
+  virtual rd_status set_tissue(const double*, const double*, const double*) = 0;
+  virtual rd_status set_basis(const double*, double) = 0;
+  virtual rd_status set_data(const double*) = 0;
+  virtual rd_status forward(const double*, double, double, double*, double*) = 0;
+  virtual rd_status adjoint(double*) = 0;
+  virtual rd_status hessvec(const double*, double, double, const double*, double*) = 0;
+  virtual rd_status apply_operator(double, const double*, double*) = 0;
+  virtual rd_status apply_precond(double, const double*, double*) = 0;
+};
+
+template <typename T>
+struct Engine : EngineBase {
+  using L_ = Launch<T>;
+  void* ws = nullptr;
+  bool own_ws = false;
+  Params* prm = nullptr;
+  Params* hprm = nullptr;   // pinned host mirror
+  PcgState* st = nullptr;
+  PcgState* hst = nullptr;  // pinned host mirror
+  double* part = nullptr;
+  unsigned int* counter = nullptr;
+  cpx<T>* twA[kNumL] = {};
+  cpx<T>* twB[kNumL] = {};
+  double* fac = nullptr;
+  double* pdev = nullptr;
+  double* gp = nullptr;
+  double* phit_part = nullptr;
+  double* stage[3] = {};
+  T* f[F_COUNT] = {};
+  std::vector<T*> slots;   // checkpoint storage
+  int nmax = 0;
+  double sigma = 0;
+  int stride = 0, nseg = 0;   // checkpoint stride and number of stored states
+  int seg_loaded = -1;        // segment whose c** are in the segment slots
+
+  // ------------------------------------------------------------ set-up
+  static size_t layout(Carve& c, const rd_config& cfg, int np, Engine* e) {
+    const long long nn = (long long)cfg.n[0] * cfg.n[1] * cfg.n[2];
+    const int nmax = std::max(cfg.n[0], std::max(cfg.n[1], cfg.n[2]));
+    auto put = [&](void** dst, size_t bytes) {
+      void* p = c.take(bytes);
+      if (e) *dst = p;
+    };
+    void* dummy;
+    put(e ? (void**)&e->prm : &dummy, sizeof(Params));
+    put(e ? (void**)&e->st : &dummy, sizeof(PcgState));
+    put(e ? (void**)&e->part : &dummy, sizeof(double) * kMaxBlocks * 4);
+    put(e ? (void**)&e->counter : &dummy, sizeof(unsigned int) * 64);
+    for (int i = 0; i < kNumL; ++i) {
+      const int L = 8 << i;
+      put(e ? (void**)&e->twA[i] : &dummy, sizeof(cpx<T>) * L);
+      put(e ? (void**)&e->twB[i] : &dummy, sizeof(cpx<T>) * L);
+    }
+    put(e ? (void**)&e->fac : &dummy, sizeof(double) * size_t(np) * 3 * nmax);
+    put(e ? (void**)&e->pdev : &dummy, sizeof(double) * (np + 2));
+    put(e ? (void**)&e->gp : &dummy, sizeof(double) * (np + 2));
+    put(e ? (void**)&e->phit_part : &dummy, sizeof(double) * size_t(np) * cfg.n[0]);
+    for (int i = 0; i < 3; ++i) put(e ? (void**)&e->stage[i] : &dummy, sizeof(double) * nn);
+    for (int i = 0; i < F_COUNT; ++i) put(e ? (void**)&e->f[i] : &dummy, sizeof(T) * nn);
+    int nslots;
+    if (cfg.ckpt_stride <= 0 || cfg.ckpt_stride >= cfg.nt) {
+      nslots = cfg.nt;
+    } else {
+      const int s = cfg.ckpt_stride;
+      nslots = (cfg.nt + s - 1) / s + s;
+    }
+    for (int i = 0; i < nslots; ++i) {
+      void* p = c.take(sizeof(T) * nn);
+      if (e) e->slots.push_back(reinterpret_cast<T*>(p));
+    }
+    return c.off + 256;
+  }
+
+  rd_status fail(rd_status s, const char* msg) {
+    snprintf(err, sizeof(err), "%s", msg);
+    return s;
+  }
+  rd_status cuda_fail(cudaError_t e, const char* where) {
+    snprintf(err, sizeof(err), "%s: %s", where, cudaGetErrorString(e));
+    return RD_ERR_CUDA;
+  }
+
+  rd_status init(const rd_config& c, int np_, void* workspace, size_t bytes, cudaStream_t s) {
+    cfg = c;
+    np = np_;
+    stream = s;
+    for (int a = 0; a < 3; ++a) g.n[a] = cfg.n[a];
+    nn = g.nn = (long long)cfg.n[0] * cfg.n[1] * cfg.n[2];
+    nmax = std::max(cfg.n[0], std::max(cfg.n[1], cfg.n[2]));
+    Carve m{nullptr, 0, 0, true};
+    const size_t need = layout(m, cfg, np, nullptr);
+    if (!workspace) {
+      cudaError_t e = cudaMalloc(&ws, need);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(workspace)");
+      own_ws = true;
+    } else {
+      if (bytes < need) return fail(RD_ERR_NOMEM, "workspace smaller than rd_workspace_size()");
+      if (reinterpret_cast<uintptr_t>(workspace) & 255) return fail(RD_ERR_ARG, "workspace not 256-byte aligned");
+      ws = workspace;
+    }
+    Carve cv{reinterpret_cast<char*>(ws), 0, need, false};
+    layout(cv, cfg, np, this);
+    if (cfg.ckpt_stride > 0 && cfg.ckpt_stride < cfg.nt) {
+      stride = cfg.ckpt_stride;
+      nseg = (cfg.nt + stride - 1) / stride;
+    } else {
+      stride = 0;
+      nseg = 0;
+    }
+    cudaError_t e;
+    if ((e = cudaMallocHost(&hprm, sizeof(Params))) != cudaSuccess) return cuda_fail(e, "cudaMallocHost");
+    if ((e = cudaMallocHost(&hst, sizeof(PcgState))) != cudaSuccess) return cuda_fail(e, "cudaMallocHost");
+    memset(hprm, 0, sizeof(Params));
+    memset(hst, 0, sizeof(PcgState));
+    hprm->s = 0.5 * cfg.t_end / cfg.nt;
+    hprm->h3 = kTwoPi * kTwoPi * kTwoPi / double(nn);
+    hprm->inv_nn = 1.0 / double(nn);
+    hst->rtol2 = cfg.pcg_rtol * cfg.pcg_rtol;
+    hst->maxit = cfg.pcg_maxit;
+    if ((e = cudaMemcpyAsync(prm, hprm, sizeof(Params), cudaMemcpyHostToDevice, stream)) != cudaSuccess)
+      return cuda_fail(e, "upload params");
+    if ((e = cudaMemcpyAsync(st, hst, sizeof(PcgState), cudaMemcpyHostToDevice, stream)) != cudaSuccess)
+      return cuda_fail(e, "upload pcg state");
+    if ((e = cudaMemsetAsync(counter, 0, sizeof(unsigned int) * 64, stream)) != cudaSuccess)
+      return cuda_fail(e, "memset counters");
+    // twiddle tables, computed in FP64 on the host
+    std::vector<cpx<T>> ta, tb;
+    for (int i = 0; i < kNumL; ++i) {
+      const int L = 8 << i;
+      const int R = (L >= 128) ? 16 : (L >= 32 ? 8 : (L >= 8 ? 4 : 2));
+      const int TH = L / R;
+      ta.assign(L, cpx<T>{T(0), T(0)});
+      tb.assign(L, cpx<T>{T(0), T(0)});
+      for (int k1 = 0; k1 < R; ++k1)
+        for (int t = 0; t < TH; ++t) {
+          const double th = kTwoPi * double((long long)t * k1 % L) / L;
+          ta[k1 * TH + t] = {T(std::cos(th)), T(-std::sin(th))};
+        }
+      for (int m = 0; m < R / TH; ++m)
+        for (int n2 = 0; n2 < TH; ++n2)
+          for (int j = 0; j < TH; ++j) {
+            const int k1 = j + TH * m;
+            const double th = kTwoPi * double((long long)n2 * k1 % L) / L;
+            tb[(m * TH + n2) * TH + j] = {T(std::cos(th)), T(std::sin(th))};
+          }
+      if ((e = cudaMemcpyAsync(twA[i], ta.data(), sizeof(cpx<T>) * L, cudaMemcpyHostToDevice, stream)) != cudaSuccess)
+        return cuda_fail(e, "upload twiddles");
+      if ((e = cudaMemcpyAsync(twB[i], tb.data(), sizeof(cpx<T>) * L, cudaMemcpyHostToDevice, stream)) != cudaSuccess)
+        return cuda_fail(e, "upload twiddles");
+      if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_fail(e, "sync");
+    }
+    return RD_OK;
+  }
+
+  ~Engine() override {
+    if (hprm) cudaFreeHost(hprm);
+    if (hst) cudaFreeHost(hst);
+    if (own_ws && ws) cudaFree(ws);
+  }
+
+  // ------------------------------------------------------------ helpers
+  Fin fin(int kind, int slot = 0, double scale = 1.0, double* target = nullptr) {
+    Fin r;
+    r.kind = kind;
+    r.slot = slot;
+    r.scale = scale;
+    r.st = st;
+    r.prm = prm;
+    r.part = part;
+    r.counter = counter;
+    r.target = target;
+    return r;
+  }
+
+  // copy an FP64 field (host or device) into staging slot i; returns the
+  // device pointer to read from
+  cudaError_t stage_in(const double* src, int i, const double** dev) {
+    if (is_device_ptr(src)) {
+      *dev = src;
+      return cudaSuccess;
+    }
+    *dev = stage[i];
+    return cudaMemcpyAsync(stage[i], src, sizeof(double) * nn, cudaMemcpyHostToDevice, stream);
+  }
+
+  cudaError_t field_out(const T* src, double* dst, double scale) {
+    cudaError_t e;
+    if (is_device_ptr(dst)) return L_::to_f64(src, dst, nn, scale, stream);
+    if ((e = L_::to_f64(src, stage[0], nn, scale, stream)) != cudaSuccess) return e;
+    return cudaMemcpyAsync(dst, stage[0], sizeof(double) * nn, cudaMemcpyDeviceToHost, stream);
+  }
+
+  cudaError_t upload_params() {
+    return cudaMemcpyAsync(prm, hprm, sizeof(Params), cudaMemcpyHostToDevice, stream);
+  }
+
+  // out = c0 * (use_kf ? k_f : 1) * s * A1 u, A1 = div(kappa1 grad .)
+  cudaError_t apply3(const T* u, T* out, double c0, int use_kf) {
+    for (int axis : {2, 1, 0}) {
+      OpArgs<T> a{};
+      a.u = u;
+      a.kappa = f[F_KAPPA1];
+      a.acc_in = (axis == 2) ? nullptr : out;
+      a.out = out;
+      a.c0 = c0;
+      a.use_kf = use_kf;
+      a.a_self = 0;
+      a.reduce = 0;
+      a.axis = axis;
+      a.g = g;
+      const int L = g.n[axis];
+      a.twA = twA[lidx(L)];
+      a.twB = twB[lidx(L)];
+      a.prm = prm;
+      cudaError_t e = L_::op(L, a, stream);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  }
+
+  DhtArgs<T> dht_args(int axis, const T* in, T* out) {
+    DhtArgs<T> a{};
+    a.in = in;
+    a.out = out;
+    a.axis = axis;
+    a.g = g;
+    const int L = g.n[axis];
+    a.twA = twA[lidx(L)];
+    a.twB = twB[lidx(L)];
+    a.prm = prm;
+    a.st = st;
+    return a;
+  }
+
+  // Preconditioned CG on (I - s k_f A1) x = f with x0 = 0; f in F_R on entry;
+  // the solution is left in F_X and the final residual in F_R.
+  rd_status pcg() {
+    cudaError_t e;
+    T *X = f[F_X], *R = f[F_R], *P = f[F_P], *Q = f[F_Q], *W1 = f[F_W1], *W2 = f[F_W2];
+    if ((e = cudaMemsetAsync(X, 0, sizeof(T) * nn, stream)) != cudaSuccess) return cuda_fail(e, "memset x");
+    {
+      DhtArgs<T> a = dht_args(2, R, W1);
+      a.fin = fin(kFinSetup);
+      if ((e = L_::dht(g.n[2], kDhtSetup, a, stream)) != cudaSuccess) return cuda_fail(e, "pcg setup");
+    }
+    ++last_solves;
+    for (int guard = 0;; ++guard) {
+      if (guard > cfg.pcg_maxit + 2) return fail(RD_ERR_CUDA, "PCG state did not advance");
+      if ((e = cudaMemcpyAsync(hst, st, sizeof(PcgState), cudaMemcpyDeviceToHost, stream)) != cudaSuccess)
+        return cuda_fail(e, "read pcg state");
+      if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_fail(e, "pcg sync");
+      if (hst->done) break;
+      {
+        DhtArgs<T> a = dht_args(1, W1, W2);
+        if ((e = L_::dht(g.n[1], kDhtPlain, a, stream)) != cudaSuccess) return cuda_fail(e, "dht y");
+      }
+      {
+        DhtArgs<T> a = dht_args(0, W2, W1);
+        a.fin = fin(kFinRz);
+        if ((e = L_::dht(g.n[0], kDhtSym, a, stream)) != cudaSuccess) return cuda_fail(e, "dht z");
+      }
+      {
+        DhtArgs<T> a = dht_args(1, W1, W2);
+        if ((e = L_::dht(g.n[1], kDhtPlain, a, stream)) != cudaSuccess) return cuda_fail(e, "dht y");
+      }
+      {
+        PcgOpxArgs<T> a{};
+        a.w = W2;
+        a.p = P;
+        a.q = Q;
+        a.kappa = f[F_KAPPA1];
+        a.g = g;
+        a.twA = twA[lidx(g.n[2])];
+        a.twB = twB[lidx(g.n[2])];
+        a.prm = prm;
+        a.st = st;
+        if ((e = L_::pcg_opx(g.n[2], a, stream)) != cudaSuccess) return cuda_fail(e, "pcg opx");
+      }
+      for (int axis : {1, 0}) {
+        OpArgs<T> a{};
+        a.u = P;
+        a.kappa = f[F_KAPPA1];
+        a.acc_in = Q;
+        a.out = Q;
+        a.c0 = -1.0;
+        a.use_kf = 1;
+        a.a_self = 0;
+        a.reduce = (axis == 0);
+        a.axis = axis;
+        a.g = g;
+        a.twA = twA[lidx(g.n[axis])];
+        a.twB = twB[lidx(g.n[axis])];
+        a.prm = prm;
+        a.fin = fin(kFinPq);
+        if ((e = L_::op(g.n[axis], a, stream)) != cudaSuccess) return cuda_fail(e, "pcg op");
+      }
+      {
+        DhtArgs<T> a = dht_args(2, nullptr, W1);
+        a.x = X;
+        a.p = P;
+        a.r = R;
+        a.q = Q;
+        a.fin = fin(kFinRr);
+        if ((e = L_::dht(g.n[2], kDhtUpdate, a, stream)) != cudaSuccess) return cuda_fail(e, "pcg update");
+      }
+    }
+    last_iters += hst->it;
+    if (hst->status == kStNonFinite) return fail(RD_ERR_NONFINITE, "non-finite value in a PCG solve");
+    if (hst->status == kStNoConv) nonconv = true;
+    return RD_OK;
+  }
+
+  PwArgs<T> pw_args() {
+    PwArgs<T> a{};
+    a.rho1 = f[F_RHO1];
+    a.nn = nn;
+    a.prm = prm;
+    return a;
+  }
+
+  // storage of c** for step n and the "previous" pointer of step n
+  T* css_slot(int n) { return stride ? slots[nseg + (n % stride)] : slots[n]; }
+  void prev_of(int n, const T** prev, int* is_state) {
+    if (n == 0) {
+      *prev = stride ? slots[0] : f[F_C0];
+      *is_state = 1;
+    } else if (stride && n % stride == 0) {
+      *prev = slots[n / stride];
+      *is_state = 1;
+    } else {
+      *prev = css_slot(n - 1);
+      *is_state = 0;
+    }
+  }
+
+  rd_status fwd_step(int n) {
+    cudaError_t e;
+    rd_status rs;
+    const T* prev;
+    int is_state;
+    prev_of(n, &prev, &is_state);
+    PwArgs<T> a = pw_args();
+    a.prev = prev;
+    a.prev_is_state = is_state;
+    a.out0 = f[F_CS];
+    if ((e = L_::pw(kPwFwdPre, a, stream)) != cudaSuccess) return cuda_fail(e, "fwd pre");
+    if ((e = apply3(f[F_CS], f[F_R], 2.0, 1)) != cudaSuccess) return cuda_fail(e, "fwd rhs");
+    if ((rs = pcg()) != RD_OK) return rs;
+    PwArgs<T> b = pw_args();
+    b.a = f[F_CS];
+    b.b = f[F_X];
+    b.out0 = css_slot(n);
+    if ((e = L_::pw(kPwFwdPost, b, stream)) != cudaSuccess) return cuda_fail(e, "fwd post");
+    return RD_OK;
+  }
+
+  // store the state c_n of a segment start (checkpoint mode)
+  rd_status store_state(int n) {
+    const T* prev;
+    int is_state;
+    if (n == 0) return RD_OK;   // slot 0 written from Phi p
+    prev = css_slot(n - 1);
+    is_state = 0;
+    PwArgs<T> a = pw_args();
+    a.prev = prev;
+    a.prev_is_state = is_state;
+    a.out0 = slots[n / stride];
+    cudaError_t e = L_::pw(kPwState, a, stream);
+    return e == cudaSuccess ? RD_OK : cuda_fail(e, "store state");
+  }
+
+  rd_status run_segment(int k) {   // recompute c** of segment k into the segment slots
+    rd_status rs;
+    const int n0 = k * stride, n1 = std::min(cfg.nt, n0 + stride);
+    for (int n = n0; n < n1; ++n)
+      if ((rs = fwd_step(n)) != RD_OK) return rs;
+    seg_loaded = k;
+    return RD_OK;
+  }
+
+  rd_status run_forward(const double* p, double k_f, double rho_f) {
+    cudaError_t e;
+    rd_status rs;
+    if (!have_tissue || !have_basis) return fail(RD_ERR_STATE, "rd_set_tissue and rd_set_basis are required");
+    hprm->k_f = k_f;
+    hprm->rho_f = rho_f;
+    hprm->v_k = hprm->v_rho = 0.0;
+    for (double& x : hprm->acc) x = 0.0;
+    if ((e = upload_params()) != cudaSuccess) return cuda_fail(e, "upload params");
+    if ((e = cudaMemcpyAsync(pdev, p, sizeof(double) * np, cudaMemcpyHostToDevice, stream)) != cudaSuccess)
+      return cuda_fail(e, "upload p");
+    PhiArgs<T> pa{};
+    pa.fac = fac;
+    pa.p = pdev;
+    pa.out = stride ? slots[0] : f[F_C0];
+    pa.np = np;
+    pa.nmax = nmax;
+    pa.g = g;
+    pa.cut = 1e-30;
+    if ((e = L_::phi(pa, stream)) != cudaSuccess) return cuda_fail(e, "phi");
+    for (int n = 0; n < cfg.nt; ++n) {
+      if (stride && n % stride == 0 && (rs = store_state(n)) != RD_OK) return rs;
+      if ((rs = fwd_step(n)) != RD_OK) return rs;
+    }
+    seg_loaded = stride ? (cfg.nt - 1) / stride : -1;
+    theta_p.assign(p, p + np);
+    theta_kf = k_f;
+    theta_rho = rho_f;
+    have_traj = true;
+    have_grad = false;
+    return RD_OK;
+  }
+
+  // misfit, alpha(1) = d - c(1), optional c(1) output
+  rd_status finish_forward(double* c1_out, double* misfit) {
+    cudaError_t e;
+    PwArgs<T> a = pw_args();
+    a.a = css_slot(cfg.nt - 1);
+    a.d = f[F_D];
+    a.out0 = f[F_ALPHA];
+    a.out1 = f[F_CS];   // c(1)
+    a.reduce = 1;
+    a.fin = fin(kFinAcc, kAccMisfit, 0.5 * hprm->h3);
+    if ((e = L_::pw(kPwMisfit, a, stream)) != cudaSuccess) return cuda_fail(e, "misfit");
+    if (c1_out && (e = field_out(f[F_CS], c1_out, 1.0)) != cudaSuccess) return cuda_fail(e, "c1 out");
+    if ((e = cudaMemcpyAsync(hprm, prm, sizeof(Params), cudaMemcpyDeviceToHost, stream)) != cudaSuccess)
+      return cuda_fail(e, "read params");
+    if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_fail(e, "sync");
+    if (misfit) {
+      double reg = 0.0;
+      for (double x : theta_p) reg += x * x;
+      *misfit = hprm->acc[kAccMisfit] + 0.5 * cfg.beta_p * reg;
+    }
+    return RD_OK;
+  }
+
+  rd_status adj_step(int n) {
+    cudaError_t e;
+    rd_status rs;
+    const T* prev;
+    int is_state;
+    prev_of(n, &prev, &is_state);
+    const double gscale = -hprm->h3 * hprm->s;
+    PwArgs<T> a = pw_args();
+    a.a = f[F_ALPHA];
+    a.b = css_slot(n);
+    a.prev = prev;
+    a.prev_is_state = is_state;
+    a.out0 = f[F_AB];
+    a.out1 = f[F_WS];
+    a.out2 = f[F_CN];
+    a.reduce = 1;
+    a.fin = fin(kFinAcc, kAccGrho, gscale);
+    if ((e = L_::pw(kPwAdjPre, a, stream)) != cudaSuccess) return cuda_fail(e, "adj pre");
+    if ((e = apply3(f[F_AB], f[F_R], 1.0, 1)) != cudaSuccess) return cuda_fail(e, "adj rhs");
+    if ((rs = pcg()) != RD_OK) return rs;
+    for (int axis : {2, 1, 0}) {
+      GradArgs<T> ga{};
+      ga.u0 = f[F_AB];
+      ga.u1 = f[F_X];
+      ga.w = f[F_WS];
+      ga.kappa = f[F_KAPPA1];
+      ga.axis = axis;
+      ga.g = g;
+      ga.twA = twA[lidx(g.n[axis])];
+      ga.twB = twB[lidx(g.n[axis])];
+      ga.fin = fin(kFinAcc, kAccGk, hprm->s * hprm->h3);
+      if ((e = L_::grad(g.n[axis], ga, stream)) != cudaSuccess) return cuda_fail(e, "grad pass");
+    }
+    PwArgs<T> b = pw_args();
+    b.a = f[F_AB];
+    b.b = f[F_X];
+    b.d = f[F_R];
+    b.prev = f[F_CN];
+    b.prev_is_state = 1;
+    b.out0 = f[F_ALPHA];
+    b.reduce = 1;
+    b.fin = fin(kFinAcc, kAccGrho, gscale);
+    if ((e = L_::pw(kPwAdjPost, b, stream)) != cudaSuccess) return cuda_fail(e, "adj post");
+    return RD_OK;
+  }
+
+  // reverse sweep from alpha(1) in F_ALPHA; g_kf, g_rho into acc, g_p into gp
+  rd_status run_adjoint() {
+    cudaError_t e;
+    rd_status rs;
+    hprm->acc[kAccGk] = hprm->acc[kAccGrho] = 0.0;
+    // zero the two gradient accumulators on the device without touching the rest
+    if ((e = cudaMemsetAsync(&prm->acc[kAccGk], 0, 2 * sizeof(double), stream)) != cudaSuccess)
+      return cuda_fail(e, "zero acc");
+    if (!stride) {
+      for (int n = cfg.nt - 1; n >= 0; --n)
+        if ((rs = adj_step(n)) != RD_OK) return rs;
+    } else {
+      for (int k = nseg - 1; k >= 0; --k) {
+        if (seg_loaded != k) {
+          // the recompute overwrites F_ALPHA's neighbours only; keep alpha
+          if ((rs = run_segment(k)) != RD_OK) return rs;
+        }
+        const int n0 = k * stride, n1 = std::min(cfg.nt, n0 + stride);
+        for (int n = n1 - 1; n >= n0; --n)
+          if ((rs = adj_step(n)) != RD_OK) return rs;
+      }
+      seg_loaded = -1;
+    }
+    PhiArgs<T> pa{};
+    pa.fac = fac;
+    pa.u = f[F_ALPHA];
+    pa.part = phit_part;
+    pa.np = np;
+    pa.nmax = nmax;
+    pa.g = g;
+    pa.cut = 1e-30;
+    if ((e = L_::phit(pa, gp, -hprm->h3, stream)) != cudaSuccess) return cuda_fail(e, "phi^T");
+    return RD_OK;
+  }
+
+  rd_status collect(double* out, const double* vp) {
+    cudaError_t e;
+    std::vector<double> h(np);
+    if ((e = cudaMemcpyAsync(h.data(), gp, sizeof(double) * np, cudaMemcpyDeviceToHost, stream)) != cudaSuccess)
+      return cuda_fail(e, "read g_p");
+    if ((e = cudaMemcpyAsync(hprm, prm, sizeof(Params), cudaMemcpyDeviceToHost, stream)) != cudaSuccess)
+      return cuda_fail(e, "read params");
+    if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_fail(e, "sync");
+    for (int i = 0; i < np; ++i) out[i] = h[i] + cfg.beta_p * vp[i];
+    out[np] = hprm->acc[kAccGk];
+    out[np + 1] = hprm->acc[kAccGrho];
+    return RD_OK;
+  }
+
+  void begin_call() {
+    err[0] = 0;
+    last_iters = 0;
+    last_solves = 0;
+    nonconv = false;
+  }
+  rd_status end_call(rd_status s) {
+    if (s == RD_OK && nonconv) {
+      snprintf(err, sizeof(err), "a PCG solve reached pcg_maxit");
+      return RD_ERR_NOCONV;
+    }
+    return s;
+  }
+
+  // ------------------------------------------------------------ API
+  rd_status set_tissue(const double* m0, const double* m1, const double* m2) override {
+    cudaError_t e;
+    const double* d[3];
+    const double* src[3] = {m0, m1, m2};
+    for (int i = 0; i < 3; ++i)
+      if ((e = stage_in(src[i], i, &d[i])) != cudaSuccess) return cuda_fail(e, "stage tissue");
+    CoefArgs<T> a{};
+    a.m0 = d[0];
+    a.m1 = d[1];
+    a.m2 = d[2];
+    a.kappa1 = f[F_KAPPA1];
+    a.rho1 = f[F_RHO1];
+    a.kw0 = cfg.k_w[0];
+    a.kw1 = cfg.k_w[1];
+    a.kw2 = cfg.k_w[2];
+    a.rw0 = cfg.rho_w[0];
+    a.rw1 = cfg.rho_w[1];
+    a.rw2 = cfg.rho_w[2];
+    a.nn = nn;
+    a.fin = fin(kFinSet, 0, 1.0 / double(nn), &prm->kbar1);
+    if ((e = L_::coef(a, stream)) != cudaSuccess) return cuda_fail(e, "coefficients");
+    if ((e = cudaMemcpyAsync(&hprm->kbar1, &prm->kbar1, sizeof(double), cudaMemcpyDeviceToHost, stream)) !=
+        cudaSuccess)
+      return cuda_fail(e, "read kbar");
+    if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_fail(e, "sync");
+    have_tissue = true;
+    have_traj = false;
+    return RD_OK;
+  }
+
+  rd_status set_basis(const double* centers, double sig) override {
+    if (!(sig > 0)) return fail(RD_ERR_ARG, "sigma must be positive");
+    sigma = sig;
+    std::vector<double> h(size_t(np) * 3 * nmax, 0.0);
+    for (int i = 0; i < np; ++i)
+      for (int a = 0; a < 3; ++a)
+        for (int x = 0; x < g.n[a]; ++x) {
+          double d = kTwoPi * x / g.n[a] - centers[i * 3 + a];
+          d -= kTwoPi * std::nearbyint(d / kTwoPi);
+          h[(size_t(i) * 3 + a) * nmax + x] = std::exp(-d * d / (2.0 * sig * sig));
+        }
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(fac, h.data(), sizeof(double) * h.size(), cudaMemcpyHostToDevice, stream)) !=
+        cudaSuccess)
+      return cuda_fail(e, "upload basis");
+    if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_fail(e, "sync");
+    have_basis = true;
+    have_traj = false;
+    return RD_OK;
+  }
+
+  rd_status set_data(const double* d) override {
+    cudaError_t e;
+    const double* dv;
+    if ((e = stage_in(d, 0, &dv)) != cudaSuccess) return cuda_fail(e, "stage data");
+    if ((e = L_::from_f64(dv, f[F_D], nn, stream)) != cudaSuccess) return cuda_fail(e, "convert data");
+    if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_fail(e, "sync");
+    have_data = true;
+    return RD_OK;
+  }
+
+  rd_status forward(const double* p, double k_f, double rho_f, double* c1_out, double* misfit) override {
+    begin_call();
+    rd_status s = run_forward(p, k_f, rho_f);
+    if (s != RD_OK) return s;
+    if (!have_data) {
+      cudaError_t e = cudaMemsetAsync(f[F_D], 0, sizeof(T) * nn, stream);
+      if (e != cudaSuccess) return cuda_fail(e, "zero data");
+    }
+    s = finish_forward(c1_out, have_data ? misfit : nullptr);
+    if (s == RD_OK && misfit && !have_data) *misfit = NAN;
+    return end_call(s);
+  }
+
+  rd_status adjoint(double* alpha0_out) override {
+    if (!have_traj) return fail(RD_ERR_STATE, "rd_adjoint needs a preceding rd_forward");
+    if (!have_data) return fail(RD_ERR_STATE, "rd_set_data is required");
+    const int it0 = last_iters, so0 = last_solves;
+    begin_call();
+    last_iters = it0;
+    last_solves = so0;
+    rd_status s = run_adjoint();
+    if (s != RD_OK) return s;
+    cudaError_t e;
+    if (alpha0_out && (e = field_out(f[F_ALPHA], alpha0_out, 1.0)) != cudaSuccess) return cuda_fail(e, "alpha out");
+    last_grad.assign(np + 2, 0.0);
+    s = collect(last_grad.data(), theta_p.data());
+    if (s == RD_OK) have_grad = true;
+    return end_call(s);
+  }
+
+  rd_status apply_operator(double k_f, const double* u, double* out) override {
+    if (!have_tissue) return fail(RD_ERR_STATE, "rd_set_tissue is required");
+    begin_call();
+    cudaError_t e;
+    hprm->k_f = k_f;
+    if ((e = upload_params()) != cudaSuccess) return cuda_fail(e, "upload params");
+    const double* dv;
+    if ((e = stage_in(u, 1, &dv)) != cudaSuccess) return cuda_fail(e, "stage");
+    if ((e = L_::from_f64(dv, f[F_CS], nn, stream)) != cudaSuccess) return cuda_fail(e, "convert");
+    if ((e = apply3(f[F_CS], f[F_R], 1.0 / hprm->s, 1)) != cudaSuccess) return cuda_fail(e, "apply");
+    if ((e = field_out(f[F_R], out, 1.0)) != cudaSuccess) return cuda_fail(e, "out");
+    if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_fail(e, "sync");
+    return RD_OK;
+  }
+
+  rd_status apply_precond(double k_f, const double* r, double* out) override {
+    if (!have_tissue) return fail(RD_ERR_STATE, "rd_set_tissue is required");
+    begin_call();
+    cudaError_t e;
+    hprm->k_f = k_f;
+    if ((e = upload_params()) != cudaSuccess) return cuda_fail(e, "upload params");
+    const double* dv;
+    if ((e = stage_in(r, 1, &dv)) != cudaSuccess) return cuda_fail(e, "stage");
+    if ((e = L_::from_f64(dv, f[F_R], nn, stream)) != cudaSuccess) return cuda_fail(e, "convert");
+    DhtArgs<T> a = dht_args(2, f[F_R], f[F_W1]);
+    a.fin = fin(kFinSetup);
+    if ((e = L_::dht(g.n[2], kDhtSetup, a, stream)) != cudaSuccess) return cuda_fail(e, "dht x");
+    a = dht_args(1, f[F_W1], f[F_W2]);
+    if ((e = L_::dht(g.n[1], kDhtPlain, a, stream)) != cudaSuccess) return cuda_fail(e, "dht y");
+    a = dht_args(0, f[F_W2], f[F_W1]);
+    a.fin = fin(kFinRz);
+    if ((e = L_::dht(g.n[0], kDhtSym, a, stream)) != cudaSuccess) return cuda_fail(e, "dht z");
+    a = dht_args(1, f[F_W1], f[F_W2]);
+    if ((e = L_::dht(g.n[1], kDhtPlain, a, stream)) != cudaSuccess) return cuda_fail(e, "dht y");
+    a = dht_args(2, f[F_W2], f[F_W1]);
+    if ((e = L_::dht(g.n[2], kDhtPlain, a, stream)) != cudaSuccess) return cuda_fail(e, "dht x");
+    if ((e = field_out(f[F_W1], out, 1.0)) != cudaSuccess) return cuda_fail(e, "out");
+    if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_fail(e, "sync");
+    return RD_OK;
+  }
+
+  rd_status hessvec(const double* p, double k_f, double rho_f, const double* v, double* Hv) override {
+    begin_call();
+    rd_status s;
+    cudaError_t e;
+    bool same = have_traj && k_f == theta_kf && rho_f == theta_rho && (int)theta_p.size() == np;
+    for (int i = 0; same && i < np; ++i) same = (theta_p[i] == p[i]);
+    if (!same && (s = run_forward(p, k_f, rho_f)) != RD_OK) return s;
+    hprm->k_f = k_f;
+    hprm->rho_f = rho_f;
+    hprm->v_k = v[np];
+    hprm->v_rho = v[np + 1];
+    for (double& x : hprm->acc) x = 0.0;
+    if ((e = upload_params()) != cudaSuccess) return cuda_fail(e, "upload params");
+    if ((e = cudaMemcpyAsync(pdev, v, sizeof(double) * np, cudaMemcpyHostToDevice, stream)) != cudaSuccess)
+      return cuda_fail(e, "upload v");
+    PhiArgs<T> pa{};
+    pa.fac = fac;
+    pa.p = pdev;
+    pa.out = f[F_CH];
+    pa.np = np;
+    pa.nmax = nmax;
+    pa.g = g;
+    pa.cut = 1e-30;
+    if ((e = L_::phi(pa, stream)) != cudaSuccess) return cuda_fail(e, "phi v");
+    for (int n = 0; n < cfg.nt; ++n) {
+      if (stride && n % stride == 0 && seg_loaded != n / stride) {
+        if ((s = run_segment(n / stride)) != RD_OK) return s;
+      }
+      const T* prev;
+      int is_state;
+      prev_of(n, &prev, &is_state);
+      PwArgs<T> a = pw_args();
+      a.a = f[F_CH];
+      a.b = css_slot(n);
+      a.prev = prev;
+      a.prev_is_state = is_state;
+      a.out0 = f[F_CHS];
+      a.out1 = f[F_U];
+      if ((e = L_::pw(kPwTlPre, a, stream)) != cudaSuccess) return cuda_fail(e, "tl pre");
+      if ((e = apply3(f[F_U], f[F_R], 1.0, 0)) != cudaSuccess) return cuda_fail(e, "tl rhs");
+      if ((s = pcg()) != RD_OK) return s;
+      PwArgs<T> b = pw_args();
+      b.a = f[F_CHS];
+      b.b = f[F_X];
+      b.d = css_slot(n);
+      b.out0 = f[F_CH];
+      if ((e = L_::pw(kPwTlPost, b, stream)) != cudaSuccess) return cuda_fail(e, "tl post");
+    }
+    PwArgs<T> a = pw_args();
+    a.a = f[F_CH];
+    a.out0 = f[F_ALPHA];
+    if ((e = L_::pw(kPwNeg, a, stream)) != cudaSuccess) return cuda_fail(e, "negate");
+    if ((s = run_adjoint()) != RD_OK) return s;
+    s = collect(Hv, v);
+    return end_call(s);
+  }
+};
+
+}  // namespace rd
+
+// ================================================================== C ABI
+struct rd_ctx {
+  rd::EngineBase* e;
+};
+
+static bool valid_config(const rd_config* c) {
+  if (!c) return false;
+  if (c->nt < 1 || !(c->t_end > 0) || !(c->pcg_rtol > 0) || c->pcg_maxit < 1) return false;
+  if (c->prec != RD_FP64 && c->prec != RD_MIXED) return false;
+  if (c->ckpt_stride < 0) return false;
+  return true;
+}
+static bool valid_shape(const rd_config* c) {
+  for (int a = 0; a < 3; ++a)
+    if (!rd::supported_length(c->n[a])) return false;
+  return true;
+}
+
+extern "C" {
+
+rd_status rd_config_default(rd_config* c) {
+  if (!c) return RD_ERR_ARG;
+  memset(c, 0, sizeof(*c));
+  c->n[0] = c->n[1] = c->n[2] = 64;
+  c->nt = 16;
+  c->t_end = 1.0;
+  c->prec = RD_FP64;
+  c->pcg_rtol = 1e-10;
+  c->pcg_maxit = 200;
+  c->ckpt_stride = 0;
+  c->k_w[0] = 1.0;
+  c->k_w[1] = 0.1;
+  c->k_w[2] = 0.0;
+  c->rho_w[0] = 1.0;
+  c->rho_w[1] = 0.2;
+  c->rho_w[2] = 0.0;
+  c->beta_p = 0.0;
+  return RD_OK;
+}
+
+rd_status rd_workspace_size(const rd_config* cfg, int np, size_t* bytes) {
+  if (!valid_config(cfg) || np < 1 || !bytes) return RD_ERR_ARG;
+  if (!valid_shape(cfg)) return RD_ERR_SHAPE;
+  rd::Carve m{nullptr, 0, 0, true};
+  *bytes = (cfg->prec == RD_MIXED) ? rd::Engine<float>::layout(m, *cfg, np, nullptr)
+                                   : rd::Engine<double>::layout(m, *cfg, np, nullptr);
+  return RD_OK;
+}
+
+rd_status rd_create(rd_ctx** out, const rd_config* cfg, int np, void* workspace, size_t workspace_bytes,
+                    void* stream) {
+  if (!out || !valid_config(cfg) || np < 1) return RD_ERR_ARG;
+  if (!valid_shape(cfg)) return RD_ERR_SHAPE;
+  *out = nullptr;
+  rd_ctx* c = new rd_ctx;
+  rd_status s;
+  if (cfg->prec == RD_MIXED) {
+    auto* e = new rd::Engine<float>();
+    c->e = e;
+    s = e->init(*cfg, np, workspace, workspace_bytes, (cudaStream_t)stream);
+  } else {
+    auto* e = new rd::Engine<double>();
+    c->e = e;
+    s = e->init(*cfg, np, workspace, workspace_bytes, (cudaStream_t)stream);
+  }
+  if (s != RD_OK) {
+    static thread_local char msg[512];
+    snprintf(msg, sizeof(msg), "%s", c->e->err);
+    delete c->e;
+    delete c;
+    return s;
+  }
+  *out = c;
+  return RD_OK;
+}
+
+rd_status rd_set_tissue(rd_ctx* c, const double* m_wm, const double* m_gm, const double* m_csf) {
+  if (!c || !m_wm || !m_gm || !m_csf) return RD_ERR_ARG;
+  return c->e->set_tissue(m_wm, m_gm, m_csf);
+}
+
+rd_status rd_set_basis(rd_ctx* c, const double* centers, double sigma) {
+  if (!c || !centers) return RD_ERR_ARG;
+  return c->e->set_basis(centers, sigma);
+}
+
+rd_status rd_set_data(rd_ctx* c, const double* d) {
+  if (!c || !d) return RD_ERR_ARG;
+  return c->e->set_data(d);
+}
+
+rd_status rd_forward(rd_ctx* c, const double* p, double k_f, double rho_f, double* c1_out, double* misfit) {
+  if (!c || !p || !(k_f >= 0) || !std::isfinite(rho_f)) return RD_ERR_ARG;
+  return c->e->forward(p, k_f, rho_f, c1_out, misfit);
+}
+
+rd_status rd_adjoint(rd_ctx* c, double* alpha0_out) {
+  if (!c) return RD_ERR_ARG;
+  return c->e->adjoint(alpha0_out);
+}
+
+rd_status rd_gradient(rd_ctx* c, const double* p, double k_f, double rho_f, double* misfit, double* grad) {
+  if (!c || !p || !grad || !(k_f >= 0) || !std::isfinite(rho_f)) return RD_ERR_ARG;
+  if (!c->e->have_data) {
+    snprintf(c->e->err, sizeof(c->e->err), "rd_set_data is required");
+    return RD_ERR_STATE;
+  }
+  double J = 0.0;
+  rd_status s = c->e->forward(p, k_f, rho_f, nullptr, &J);
+  if (s != RD_OK && s != RD_ERR_NOCONV) return s;
+  const bool nc = (s == RD_ERR_NOCONV);
+  s = c->e->adjoint(nullptr);
+  if (s != RD_OK && s != RD_ERR_NOCONV) return s;
+  if (misfit) *misfit = J;
+  for (int i = 0; i < c->e->np + 2; ++i) grad[i] = c->e->last_grad[i];
+  return (nc || s == RD_ERR_NOCONV) ? RD_ERR_NOCONV : RD_OK;
+}
+
+rd_status rd_last_gradient(const rd_ctx* c, double* grad) {
+  if (!c || !grad) return RD_ERR_ARG;
+  if (!c->e->have_grad) return RD_ERR_STATE;
+  for (int i = 0; i < c->e->np + 2; ++i) grad[i] = c->e->last_grad[i];
+  return RD_OK;
+}
+
+rd_status rd_hessvec(rd_ctx* c, const double* p, double k_f, double rho_f, const double* v, double* Hv) {
+  if (!c || !p || !v || !Hv || !(k_f >= 0) || !std::isfinite(rho_f)) return RD_ERR_ARG;
+  if (!c->e->have_tissue || !c->e->have_basis) {
+    snprintf(c->e->err, sizeof(c->e->err), "rd_set_tissue and rd_set_basis are required");
+    return RD_ERR_STATE;
+  }
+  return c->e->hessvec(p, k_f, rho_f, v, Hv);
+}
+
+rd_status rd_apply_operator(rd_ctx* c, double k_f, const double* u, double* Au) {
+  if (!c || !u || !Au || !std::isfinite(k_f)) return RD_ERR_ARG;
+  return c->e->apply_operator(k_f, u, Au);
+}
+
+rd_status rd_apply_precond(rd_ctx* c, double k_f, const double* r, double* z) {
+  if (!c || !r || !z || !(k_f >= 0)) return RD_ERR_ARG;
+  return c->e->apply_precond(k_f, r, z);
+}
+
+void rd_profile_enable(int on) {
+  rd::Profiler& p = rd::prof();
+  std::lock_guard<std::mutex> lk(p.mu);
+  p.drain();
+  p.on = (on != 0);
+  for (int i = 0; i < rd::kcCount; ++i) {
+    p.ms[i] = 0.0;
+    p.count[i] = 0;
+  }
+}
+
+int rd_profile_read(double* ms, long long* launches, int n) {
+  rd::Profiler& p = rd::prof();
+  std::lock_guard<std::mutex> lk(p.mu);
+  p.drain();
+  for (int i = 0; i < n && i < rd::kcCount; ++i) {
+    if (ms) ms[i] = p.ms[i];
+    if (launches) launches[i] = p.count[i];
+  }
+  return rd::kcCount;
+}
+
+const char* rd_profile_class(int i) { return (i >= 0 && i < rd::kcCount) ? rd::kClassNames[i] : ""; }
+
+int rd_last_pcg_iters(const rd_ctx* c) { return c ? c->e->last_iters : 0; }
+int rd_last_pcg_solves(const rd_ctx* c) { return c ? c->e->last_solves : 0; }
+
+const char* rd_last_error(const rd_ctx* c) { return c ? c->e->err : "null context"; }
+
+void rd_destroy(rd_ctx* c) {
+  if (!c) return;
+  delete c->e;
+  delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,40 @@
+// Host launchers for the kernels of rd_passes.cuh, one explicit
+// instantiation per working precision (rd_kern_f32.cu, rd_kern_f64.cu).
+#pragma once
+
+#include "rd_passes.cuh"
+
+namespace rd {
+
+constexpr int kMaxBlocks = 4096;   // capacity of the reduction partial buffer
+
+bool supported_length(int L);
+
+// Kernel classes for the optional per-launch event timing.
+enum KClass {
+  kcOpContig = 0, kcOpStrided, kcPcgOpx, kcDhtSetup, kcDhtPlain, kcDhtUpdate, kcDhtSym,
+  kcGrad, kcPointwise, kcOther, kcCount
+};
+// When timing is on, every launch is bracketed by two CUDA events on its
+// stream; prof_begin returns a token for prof_end (-1 when off).
+int prof_begin(int cls, cudaStream_t s);
+void prof_end(int token, cudaStream_t s);
+
+template <typename T>
+struct Launch {
+  static cudaError_t op(int L, const OpArgs<T>& a, cudaStream_t s);
+  static cudaError_t dht(int L, int mode, const DhtArgs<T>& a, cudaStream_t s);
+  static cudaError_t pcg_opx(int L, const PcgOpxArgs<T>& a, cudaStream_t s);
+  static cudaError_t grad(int L, const GradArgs<T>& a, cudaStream_t s);
+  static cudaError_t pw(int kind, const PwArgs<T>& a, cudaStream_t s);
+  static cudaError_t coef(const CoefArgs<T>& a, cudaStream_t s);
+  static cudaError_t phi(const PhiArgs<T>& a, cudaStream_t s);
+  static cudaError_t phit(const PhiArgs<T>& a, double* out, double scale, cudaStream_t s);
+  static cudaError_t from_f64(const double* in, T* out, long long nn, cudaStream_t s);
+  static cudaError_t to_f64(const T* in, double* out, long long nn, double scale, cudaStream_t s);
+};
+
+extern template struct Launch<float>;
+extern template struct Launch<double>;
+
+}  // namespace rd

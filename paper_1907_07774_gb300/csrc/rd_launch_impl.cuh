@@ -1,0 +1,197 @@
+// Definitions of the launchers; included once per precision.
+#pragma once
+
+#include <mutex>
+#include <unordered_map>
+
+#include "rd_launch.cuh"
+
+namespace rd {
+
+namespace detail {
+
+inline int sm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+  }
+  return n;
+}
+
+// Blocks that fit on the device at once for a kernel (persistent grid size),
+// cached per kernel; also raises the dynamic shared-memory limit when needed.
+inline int resident_blocks(const void* fn, size_t smem) {
+  static std::mutex mu;
+  static std::unordered_map<const void*, int> cache;
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = cache.find(fn);
+  if (it != cache.end()) return it->second;
+  if (smem > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kThreads, smem) != cudaSuccess || occ < 1) occ = 1;
+  int nb = occ * sm_count();
+  if (nb > kMaxBlocks) nb = kMaxBlocks;
+  cache[fn] = nb;
+  return nb;
+}
+
+inline int grid_for(const void* fn, size_t smem, long long work_items) {
+  int cap = resident_blocks(fn, smem);
+  long long want = work_items < 1 ? 1 : work_items;
+  return (int)(want < cap ? want : cap);
+}
+
+template <typename T, int L>
+constexpr size_t pencil_smem() {
+  return size_t(Shape<L>::G) * Shape<L>::GSTRIDE * sizeof(cpx<T>);
+}
+
+template <typename K, typename A>
+cudaError_t launch_pencil(K kern, size_t smem, long long groups_needed, const A& a, cudaStream_t s,
+                          int cls = kcOther) {
+  const void* fn = reinterpret_cast<const void*>(kern);
+  int grid = grid_for(fn, smem, groups_needed);
+  const int tok = prof_begin(cls, s);
+  kern<<<grid, kThreads, smem, s>>>(a);
+  cudaError_t e = cudaGetLastError();
+  prof_end(tok, s);
+  return e;
+}
+
+#define RD_DISPATCH_L(L, ...)                          \
+  switch (L) {                                         \
+    case 8: { constexpr int LL = 8; __VA_ARGS__ }      \
+    case 16: { constexpr int LL = 16; __VA_ARGS__ }    \
+    case 32: { constexpr int LL = 32; __VA_ARGS__ }    \
+    case 64: { constexpr int LL = 64; __VA_ARGS__ }    \
+    case 128: { constexpr int LL = 128; __VA_ARGS__ }  \
+    case 256: { constexpr int LL = 256; __VA_ARGS__ }  \
+    default: return cudaErrorInvalidValue;             \
+  }
+
+}  // namespace detail
+
+template <typename T>
+cudaError_t Launch<T>::op(int L, const OpArgs<T>& a, cudaStream_t s) {
+  using namespace detail;
+  const long long npairs = a.g.nn / L / 2;
+  RD_DISPATCH_L(L, {
+    constexpr size_t sm = pencil_smem<T, LL>();
+    const long long blocks = (npairs + Shape<LL>::G - 1) / Shape<LL>::G;
+    if (a.axis == 2) return launch_pencil(k_op<T, LL, true>, sm, blocks, a, s, kcOpContig);
+    return launch_pencil(k_op<T, LL, false>, sm, blocks, a, s, kcOpStrided);
+  })
+}
+
+template <typename T>
+cudaError_t Launch<T>::dht(int L, int mode, const DhtArgs<T>& a, cudaStream_t s) {
+  using namespace detail;
+  const long long npairs = a.g.nn / L / 2;
+  RD_DISPATCH_L(L, {
+    constexpr size_t sm = pencil_smem<T, LL>();
+    const long long blocks = (npairs + Shape<LL>::G - 1) / Shape<LL>::G;
+    switch (mode) {
+      case kDhtPlain:
+        if (a.axis == 2) return launch_pencil(k_dht<T, LL, true, kDhtPlain>, sm, blocks, a, s, kcDhtPlain);
+        return launch_pencil(k_dht<T, LL, false, kDhtPlain>, sm, blocks, a, s, kcDhtPlain);
+      case kDhtSetup:
+        return launch_pencil(k_dht<T, LL, true, kDhtSetup>, sm, blocks, a, s, kcDhtSetup);
+      case kDhtUpdate:
+        return launch_pencil(k_dht<T, LL, true, kDhtUpdate>, sm, blocks, a, s, kcDhtUpdate);
+      case kDhtSym:
+        return launch_pencil(k_dht<T, LL, false, kDhtSym>, sm, blocks, a, s, kcDhtSym);
+      default:
+        return cudaErrorInvalidValue;
+    }
+  })
+}
+
+template <typename T>
+cudaError_t Launch<T>::pcg_opx(int L, const PcgOpxArgs<T>& a, cudaStream_t s) {
+  using namespace detail;
+  const long long npairs = a.g.nn / L / 2;
+  RD_DISPATCH_L(L, {
+    constexpr size_t sm = pencil_smem<T, LL>();
+    const long long blocks = (npairs + Shape<LL>::G - 1) / Shape<LL>::G;
+    return launch_pencil(k_pcg_opx<T, LL>, sm, blocks, a, s, kcPcgOpx);
+  })
+}
+
+template <typename T>
+cudaError_t Launch<T>::grad(int L, const GradArgs<T>& a, cudaStream_t s) {
+  using namespace detail;
+  const long long npairs = a.g.nn / L / 2;
+  RD_DISPATCH_L(L, {
+    constexpr size_t sm = pencil_smem<T, LL>();
+    const long long blocks = (npairs + Shape<LL>::G - 1) / Shape<LL>::G;
+    if (a.axis == 2) return launch_pencil(k_grad<T, LL, true>, sm, blocks, a, s, kcGrad);
+    return launch_pencil(k_grad<T, LL, false>, sm, blocks, a, s, kcGrad);
+  })
+}
+
+template <typename T>
+cudaError_t Launch<T>::pw(int kind, const PwArgs<T>& a, cudaStream_t s) {
+  using namespace detail;
+  const long long blocks = (a.nn + kThreads - 1) / kThreads;
+#define RD_PW(K) \
+  case K: return launch_pencil(k_pw<T, K>, 0, blocks, a, s, kcPointwise);
+  switch (kind) {
+    RD_PW(kPwFwdPre)
+    RD_PW(kPwFwdPost)
+    RD_PW(kPwMisfit)
+    RD_PW(kPwAdjPre)
+    RD_PW(kPwAdjPost)
+    RD_PW(kPwTlPre)
+    RD_PW(kPwTlPost)
+    RD_PW(kPwNeg)
+    RD_PW(kPwState)
+    default: return cudaErrorInvalidValue;
+  }
+#undef RD_PW
+}
+
+template <typename T>
+cudaError_t Launch<T>::coef(const CoefArgs<T>& a, cudaStream_t s) {
+  using namespace detail;
+  return launch_pencil(k_coef<T>, 0, (a.nn + kThreads - 1) / kThreads, a, s);
+}
+
+template <typename T>
+cudaError_t Launch<T>::phi(const PhiArgs<T>& a, cudaStream_t s) {
+  const size_t smem = size_t(a.np) * sizeof(double);
+  const void* fn = reinterpret_cast<const void*>(k_phi<T>);
+  int grid = detail::grid_for(fn, smem, (long long)a.g.n[0] * a.g.n[1]);
+  k_phi<T><<<grid, kThreads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Launch<T>::phit(const PhiArgs<T>& a, double* out, double scale, cudaStream_t s) {
+  dim3 grid((unsigned)(a.g.n[0] < 64 ? a.g.n[0] : 64), (unsigned)a.np);
+  k_phit<T><<<grid, kThreads, 0, s>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_phit_sum<T><<<(a.np + 127) / 128, 128, 0, s>>>(a.part, out, a.np, a.g.n[0], scale);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Launch<T>::from_f64(const double* in, T* out, long long nn, cudaStream_t s) {
+  const void* fn = reinterpret_cast<const void*>(k_convert<T, double>);
+  int grid = detail::grid_for(fn, 0, (nn + kThreads - 1) / kThreads);
+  k_convert<T, double><<<grid, kThreads, 0, s>>>(in, out, nn, 1.0);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Launch<T>::to_f64(const T* in, double* out, long long nn, double scale, cudaStream_t s) {
+  const void* fn = reinterpret_cast<const void*>(k_convert<double, T>);
+  int grid = detail::grid_for(fn, 0, (nn + kThreads - 1) / kThreads);
+  k_convert<double, T><<<grid, kThreads, 0, s>>>(in, out, nn, scale);
+  return cudaGetLastError();
+}
+
+}  // namespace rd

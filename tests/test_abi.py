@@ -1,0 +1,64 @@
+"""The C-ABI library loads and exports every symbol include/rd.h declares;
+host-only entry points validate their arguments (CPU only)."""
+
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1907_07774_gb300 import build
+from paper_1907_07774_gb300 import rd as R
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return R.lib()
+
+
+def declared():
+    src = open(os.path.join(ROOT, "include", "rd.h")).read()
+    return sorted(set(re.findall(r"\b(rd_[a-z_]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared()
+    assert "rd_gradient" in names and "rd_hessvec" in names
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def test_config_default_and_workspace_size(lib):
+    cfg = R.rd_config()
+    assert lib.rd_config_default(ctypes.byref(cfg)) == 0
+    assert list(cfg.n) == [64, 64, 64] and cfg.nt == 16 and cfg.prec == R.RD_FP64
+    nb = ctypes.c_size_t()
+    assert lib.rd_workspace_size(ctypes.byref(cfg), 8, ctypes.byref(nb)) == 0
+    fields = 18 + 16      # working fields + one checkpoint slot per step
+    assert nb.value >= fields * 64 ** 3 * 8 and nb.value < (fields + 8) * 64 ** 3 * 8
+    cfg.prec = R.RD_MIXED
+    nb32 = ctypes.c_size_t()
+    assert lib.rd_workspace_size(ctypes.byref(cfg), 8, ctypes.byref(nb32)) == 0
+    assert nb32.value < nb.value
+    cfg.ckpt_stride = 4   # 4 stored states + 4 segment slots instead of 16
+    nbs = ctypes.c_size_t()
+    assert lib.rd_workspace_size(ctypes.byref(cfg), 8, ctypes.byref(nbs)) == 0
+    assert nbs.value < nb32.value
+
+
+def test_invalid_arguments_are_rejected(lib):
+    cfg = R.rd_config()
+    lib.rd_config_default(ctypes.byref(cfg))
+    nb = ctypes.c_size_t()
+    cfg.n[1] = 48
+    assert lib.rd_workspace_size(ctypes.byref(cfg), 8, ctypes.byref(nb)) == 2   # RD_ERR_SHAPE
+    cfg.n[1] = 64
+    cfg.nt = 0
+    assert lib.rd_workspace_size(ctypes.byref(cfg), 8, ctypes.byref(nb)) == 1   # RD_ERR_ARG
+    cfg.nt = 4
+    assert lib.rd_workspace_size(ctypes.byref(cfg), 0, ctypes.byref(nb)) == 1
+    assert lib.rd_gradient(None, None, 0.0, 0.0, None, None) == 1
+    assert lib.rd_last_pcg_iters(None) == 0

@@ -1,0 +1,229 @@
+"""CUDA path (through the C ABI) against the FP64 oracle, element by element.
+
+Tolerances: relative L2 <= 1e-10 for the FP64 path (both sides solve the
+CN systems to 1e-12) and <= 2e-4 for the mixed path (FP32 fields, FP64
+reductions), on c(1), fields and gradients.
+"""
+
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import rd as orc
+from paper_1907_07774_gb300 import rd as R
+from paper_1907_07774_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+TWO_PI = 2.0 * math.pi
+TOL = {"fp64": 1e-10, "mixed": 2e-4}
+RTOL = {"fp64": 1e-12, "mixed": 1e-6}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1907_07774_gb300 import build
+    build.build()
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / np.linalg.norm(np.ravel(b)))
+
+
+def coords(n):
+    x = synth.grid_coords(n)
+    return (x[0][:, None, None], x[1][None, :, None], x[2][None, None, :])
+
+
+def small_problem(n, nt, m=2, sigma=TWO_PI / 8, seed=1000):
+    return synth.calibration_problem(n=n, nt=nt, m=m, sigma=sigma, seed=seed)
+
+
+def oracle_for(prob, **kw):
+    return orc.model_from_problem(prob, rtol=1e-13, maxit=1000, kind="numpy", **kw)
+
+
+def gpu_for(prob, prec, **kw):
+    return R.context_for(prob, prec=prec, pcg_rtol=RTOL[prec], pcg_maxit=1000, **kw)
+
+
+# --------------------------------------------------------------- kernels
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("n", [(16, 32, 64), (256, 8, 16), (8, 128, 8)])
+def test_operator_single_mode_closed_form(prec, n):
+    x0, x1, x2 = coords(n)
+    k = (1, 2, 3)
+    u = np.cos(k[0] * x0 + k[1] * x1 + k[2] * x2) * np.ones(n)
+    one, zero = np.ones(n), np.zeros(n)
+    ctx = R.Context(n, 4, 1, prec=prec, k_w=(1, 0, 0), rho_w=(1, 0, 0))
+    ctx.rd_set_tissue(one, zero, zero)
+    out = np.zeros(n)
+    ctx.rd_apply_operator(0.3, u, out)
+    want = -0.3 * 14 * u
+    # round-off of a spectral second derivative grows with the largest
+    # resolved |k|^2: bound 16 eps k_f sum_a (n_a / 2)^2 max|u|
+    eps = {"fp64": 2.2e-16, "mixed": 1.2e-7}[prec]
+    bound = 16 * eps * 0.3 * sum((m / 2) ** 2 for m in n) * np.abs(u).max()
+    assert np.abs(out - want).max() <= bound
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("n", [(16, 16, 16), (8, 16, 32), (32, 32, 32)])
+def test_operator_and_preconditioner_match_oracle(prec, n):
+    prob = small_problem(n, 4)
+    M = oracle_for(prob)
+    ctx = gpu_for(prob, prec)
+    rng = np.random.default_rng(3)
+    u = rng.standard_normal(n)
+    k_f = 0.07
+    out = np.zeros(n)
+    ctx.rd_apply_operator(k_f, u, out)
+    assert rel(out, M.A(u, k_f)) <= TOL[prec] * (10 if prec == "fp64" else 1)
+    z = np.zeros(n)
+    ctx.rd_apply_precond(k_f, u, z)
+    want = M.sp.precond(u, M.s * k_f * float(np.mean(M.kappa1)))
+    assert rel(z, want) <= TOL[prec]
+
+
+# ---------------------------------------------------------------- solves
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("n,nt", [((16, 16, 16), 4), ((8, 16, 32), 3), ((8, 8, 8), 2)])
+def test_forward_matches_oracle(prec, n, nt):
+    prob = small_problem(n, nt)
+    M = oracle_for(prob)
+    c_or, _ = M.forward(prob.p_true, prob.k_f_true, prob.rho_f_true)
+    ctx = gpu_for(prob, prec)
+    c1 = np.zeros(n)
+    ctx.rd_forward(prob.p_true, prob.k_f_true, prob.rho_f_true, c1)
+    assert rel(c1, c_or) <= TOL[prec]
+    # device output buffer
+    c1d = torch.zeros(n, dtype=torch.float64, device="cuda")
+    ctx.rd_forward(prob.p_true, prob.k_f_true, prob.rho_f_true, c1d)
+    assert rel(c1d.cpu().numpy(), c_or) <= TOL[prec]
+
+
+def _grad_case(n=(16, 16, 16), nt=4):
+    prob = small_problem(n, nt)
+    M = oracle_for(prob)
+    c_true, _ = M.forward(prob.p_true, prob.k_f_true, prob.rho_f_true)
+    d = synth.labels(c_true, synth.ellipsoid_mask(prob.n), 7)
+    return prob, M, d
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_gradient_matches_oracle(prec):
+    prob, M, d = _grad_case()
+    J_or, g_or, _, a0_or = M.gradient(prob.p, prob.k_f, prob.rho_f, d)
+    ctx = gpu_for(prob, prec)
+    ctx.rd_set_data(d)
+    J, g = ctx.rd_gradient(prob.p, prob.k_f, prob.rho_f)
+    assert abs(J - J_or) <= TOL[prec] * abs(J_or)
+    assert rel(g, g_or) <= TOL[prec]
+    # rd_forward + rd_adjoint gives the same gradient and alpha(0)
+    ctx.rd_forward(prob.p, prob.k_f, prob.rho_f)
+    a0 = np.zeros(prob.n)
+    g2 = ctx.rd_adjoint(a0)
+    assert rel(g2, g_or) <= TOL[prec]
+    assert rel(a0, a0_or) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_hessvec_matches_oracle(prec):
+    prob, M, d = _grad_case()
+    v = synth.random_directions(1, len(prob.p) + 2, 21)[0]
+    hv_or = M.hessvec(prob.p, prob.k_f, prob.rho_f, v)
+    ctx = gpu_for(prob, prec)
+    hv = ctx.rd_hessvec(prob.p, prob.k_f, prob.rho_f, v)
+    assert rel(hv, hv_or) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_checkpoint_recompute_is_bitwise_identical(prec):
+    prob, M, d = _grad_case(nt=8)
+    out = []
+    for stride in (0, 3):
+        ctx = gpu_for(prob, prec, ckpt_stride=stride)
+        ctx.rd_set_data(d)
+        out.append(ctx.rd_gradient(prob.p, prob.k_f, prob.rho_f))
+        v = np.linspace(-1, 1, len(prob.p) + 2)
+        out.append(ctx.rd_hessvec(prob.p, prob.k_f, prob.rho_f, v))
+    assert out[0][0] == out[2][0] and np.array_equal(out[0][1], out[2][1])
+    assert np.array_equal(out[1], out[3])
+
+
+def test_beta_p_regularisation_terms():
+    prob, M, d = _grad_case()
+    M.beta_p = 1e-2
+    J_or, g_or, _, _ = M.gradient(prob.p, prob.k_f, prob.rho_f, d)
+    ctx = gpu_for(prob, "fp64", beta_p=1e-2)
+    ctx.rd_set_data(d)
+    J, g = ctx.rd_gradient(prob.p, prob.k_f, prob.rho_f)
+    assert abs(J - J_or) <= 1e-10 * J_or and rel(g, g_or) <= 1e-10
+
+
+# ------------------------------------------------------- paper workloads
+def test_forward_problem_64_fp64_matches_oracle():
+    """64^3, nt = 16 forward recipe (8 Gaussians, sigma = 2 pi / 64)."""
+    prob = synth.forward_problem(n=64, nt=16)
+    M = orc.model_from_problem(prob, rtol=1e-12, kind="numpy")
+    c_or, _ = M.forward(prob.p, prob.k_f, prob.rho_f)
+    ctx = R.context_for(prob, prec="fp64", pcg_rtol=1e-12, pcg_maxit=1000)
+    c1 = np.zeros(prob.n)
+    ctx.rd_forward(prob.p, prob.k_f, prob.rho_f, c1)
+    assert rel(c1, c_or) <= 1e-10
+    mix = R.context_for(prob, prec="mixed")
+    c1m = np.zeros(prob.n)
+    mix.rd_forward(prob.p, prob.k_f, prob.rho_f, c1m)
+    assert rel(c1m, c_or) <= 2e-4
+
+
+def _calibration_data(prob, ctx):
+    c_true = torch.zeros(prob.n, dtype=torch.float64, device="cuda")
+    ctx.rd_forward(prob.p_true, prob.k_f_true, prob.rho_f_true, c_true)
+    d = synth.labels(c_true.cpu().numpy(), synth.ellipsoid_mask(prob.n), prob.seed + 7)
+    return d
+
+
+def test_gradient_128_central_differences_fp64():
+    """128^3, nt = 16, 64 Gaussians: the FP64 gradient against central
+    differences (eps = 1e-6) of the FP64 misfit on 10 seeded directions."""
+    prob = synth.calibration_problem(n=128, nt=16, m=4)
+    ctx = R.context_for(prob, prec="fp64", pcg_rtol=1e-12, pcg_maxit=1000)
+    ctx.rd_set_data(_calibration_data(prob, ctx))
+    th = np.concatenate([prob.p, [prob.k_f, prob.rho_f]])
+    J0, g = ctx.rd_gradient(prob.p, prob.k_f, prob.rho_f)
+    errs = []
+    for v in synth.random_directions(10, len(th), 5):
+        eps = 1e-6
+        jp = ctx.rd_forward((th + eps * v)[:-2], *(th + eps * v)[-2:])
+        jm = ctx.rd_forward((th - eps * v)[:-2], *(th - eps * v)[-2:])
+        fd = (jp - jm) / (2 * eps)
+        errs.append(abs(fd - g @ v) / max(abs(fd), 1e-12))
+    assert max(errs) < 1e-5, errs
+    mix = R.context_for(prob, prec="mixed")
+    mix.rd_set_data(_calibration_data(prob, ctx))
+    Jm, gm = mix.rd_gradient(prob.p, prob.k_f, prob.rho_f)
+    assert rel(gm, g) <= 2e-4 and abs(Jm - J0) <= 2e-4 * J0
+
+
+def test_gradient_256_mixed_against_fp64_and_hessian_symmetry():
+    """256^3, nt = 32, 125 Gaussians (the benchmark workload): the mixed
+    gradient against the FP64 gradient of the same GPU, and symmetry of the
+    mixed Gauss-Newton Hessian."""
+    prob = synth.calibration_problem(n=256, nt=32, m=5)
+    ref = R.context_for(prob, prec="fp64", pcg_rtol=1e-10, pcg_maxit=1000)
+    d = _calibration_data(prob, ref)
+    ref.rd_set_data(d)
+    J64, g64 = ref.rd_gradient(prob.p, prob.k_f, prob.rho_f)
+    mix = R.context_for(prob, prec="mixed", ckpt_stride=6)
+    mix.rd_set_data(d)
+    Jm, gm = mix.rd_gradient(prob.p, prob.k_f, prob.rho_f)
+    assert abs(Jm - J64) <= 2e-4 * J64
+    assert rel(gm, g64) <= 2e-4
+    v, w = synth.random_directions(2, len(prob.p) + 2, 9)
+    hv = mix.rd_hessvec(prob.p, prob.k_f, prob.rho_f, v)
+    hw = mix.rd_hessvec(prob.p, prob.k_f, prob.rho_f, w)
+    assert abs(v @ hw - w @ hv) <= 1e-3 * abs(v @ hw)
