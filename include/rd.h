@@ -139,6 +139,22 @@ rd_status rd_hessvec(rd_ctx* ctx, const double* p, double k_f, double rho_f, con
 rd_status rd_apply_operator(rd_ctx* ctx, double k_f, const double* u, double* Au);
 rd_status rd_apply_precond(rd_ctx* ctx, double k_f, const double* r, double* z);
 
+/* Allocation-free preconditioner application (the paper has no counterpart;
+ * it exists for callers that cannot allocate device memory where they need
+ * it: applications whose device memory belongs to another framework's pool,
+ * and latency-critical loops that must not pay cudaMalloc's implicit device
+ * synchronisation).  Computes z = F^-1 [F r / (1 + coef |k~|^2)] (the PCG
+ * preconditioner above with coef = tau/2 k_f mean(kappa1)) for FP64 device
+ * fields r and z on grid n[0] x n[1] x n[2] (each 8..256, a power of two;
+ * RD_ERR_SHAPE otherwise), ordered on `stream`.  No context, no workspace: the
+ * solver scalars, reduction partials and twiddle tables live in one fixed
+ * 128 KiB __device__ array of the library, held by every GPU that loads it
+ * until exit.  The first call on a device finds that array's address and
+ * uploads the tables (synchronously); make that first call before any stream
+ * capture.  All calls share the array, so calls that overlap on the GPU race;
+ * order them on one stream.  r is not modified; z may not alias r. */
+rd_status rd_apply_precond_static(const int n[3], double coef, const double* r, double* z, void* stream);
+
 /* Counters of the last call: PCG iterations summed over its solves, and
  * the number of solves. */
 int rd_last_pcg_iters(const rd_ctx* ctx);

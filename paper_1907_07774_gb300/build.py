@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "librd.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
-SOURCES = ["rd_kern_f32.cu", "rd_kern_f64.cu", "rd_api.cu"]
+SOURCES = ["rd_kern_f32.cu", "rd_kern_f64.cu", "rd_api.cu", "rd_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE]
 

@@ -62,6 +62,7 @@ def lib():
         "rd_last_pcg_solves": ([vp], ci),
         "rd_last_error": ([vp], ctypes.c_char_p),
         "rd_destroy": ([vp], None),
+        "rd_apply_precond_static": ([vp, cd, vp, vp, vp], st),
         "rd_profile_enable": ([ci], None),
         "rd_profile_read": ([vp, vp, ci], ci),
         "rd_profile_class": ([ci], ctypes.c_char_p),
@@ -85,6 +86,16 @@ def rd_profile_read():
     cnt = (ctypes.c_longlong * n)()
     k = lib().rd_profile_read(ms, cnt, n)
     return {lib().rd_profile_class(i).decode(): (ms[i], cnt[i]) for i in range(k)}
+
+
+def rd_apply_precond_static(n, coef, r, z, stream=None):
+    """Allocation-free preconditioner application (FP64 device tensors r,
+    z); see include/rd.h.  Returns the status code."""
+    import torch
+    dims = (ctypes.c_int * 3)(*[int(k) for k in n])
+    (a, ka), (b, kb) = _ptr(r), _ptr(z)
+    st = stream if stream is not None else torch.cuda.current_stream()
+    return lib().rd_apply_precond_static(dims, float(coef), a, b, ctypes.c_void_p(st.cuda_stream))
 
 
 class RDError(RuntimeError):
