@@ -14,7 +14,9 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <string>
 #include <vector>
 
@@ -67,6 +69,56 @@ Profiler& prof() {
 const char* kClassNames[kcCount] = {"op_axis2",   "op_axis01",  "pcg_opx", "dht_setup", "dht_plain",
                                     "dht_update", "dht_sym",    "grad",    "pointwise", "other"};
 }  // namespace
+
+bool strided_map(CUtensorMap* out, const void* ptr, const Geom& g, int esz, int axis) {
+  using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+  struct Key {
+    uintptr_t p;
+    int n0, n1, n2, esz, axis;
+    bool operator<(const Key& o) const {
+      return std::tie(p, n0, n1, n2, esz, axis) < std::tie(o.p, o.n0, o.n1, o.n2, o.esz, o.axis);
+    }
+  };
+  static std::mutex mu;
+  static EncodeFn fn = nullptr;
+  static bool tried = false;
+  static std::map<Key, CUtensorMap> cache;
+  std::lock_guard<std::mutex> lk(mu);
+  const Key key{reinterpret_cast<uintptr_t>(ptr), g.n[0], g.n[1], g.n[2], esz, axis};
+  auto it = cache.find(key);
+  if (it != cache.end()) {
+    *out = it->second;
+    return true;
+  }
+  if (!tried) {
+    tried = true;
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeFn>(f);
+    else
+      cudaGetLastError();
+  }
+  if (!fn || (axis != 0 && axis != 1)) return false;
+  const int W = 64 / esz;
+  const cuuint64_t dims[3] = {(cuuint64_t)g.n[2], (cuuint64_t)g.n[1], (cuuint64_t)g.n[0]};
+  const cuuint64_t strides[2] = {(cuuint64_t)g.n[2] * esz, (cuuint64_t)g.n[1] * g.n[2] * esz};
+  const cuuint32_t box[3] = {(cuuint32_t)W, (cuuint32_t)(axis == 1 ? g.n[1] : 1),
+                             (cuuint32_t)(axis == 0 ? g.n[0] : 1)};
+  const cuuint32_t es[3] = {1, 1, 1};
+  CUtensorMap m;
+  CUresult r = fn(&m, esz == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3,
+                  const_cast<void*>(ptr), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return false;
+  if (cache.size() > 4096) cache.clear();
+  cache[key] = m;
+  *out = m;
+  return true;
+}
 
 int prof_begin(int cls, cudaStream_t s) {
   Profiler& p = prof();
@@ -353,6 +405,7 @@ struct Engine : EngineBase {
       a.twA = twA[lidx(L)];
       a.twB = twB[lidx(L)];
       a.prm = prm;
+      a.fin = fin(kFinNone);
       cudaError_t e = L_::op(L, a, stream);
       if (e != cudaSuccess) return e;
     }
@@ -390,6 +443,7 @@ struct Engine : EngineBase {
       if ((e = cudaMemcpyAsync(hst, st, sizeof(PcgState), cudaMemcpyDeviceToHost, stream)) != cudaSuccess)
         return cuda_fail(e, "read pcg state");
       if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_fail(e, "pcg sync");
+      if (hst->status == kStTimeout) return fail(RD_ERR_CUDA, "a TMA wait timed out");
       if (hst->done) break;
       {
         DhtArgs<T> a = dht_args(1, W1, W2);

@@ -154,9 +154,10 @@ __device__ __forceinline__ void finalize(const Fin& f, double tot) {
 // on block scheduling.
 template <int K>
 __device__ __forceinline__ void reduce_finish(double (&v)[K], const Fin& f) {
-  __shared__ double s[K][kWarps];
+  __shared__ double s[K][32];
   __shared__ int last;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int nw = (blockDim.x + 31) >> 5;
 #pragma unroll
   for (int k = 0; k < K; ++k) {
     double t = warp_sum(v[k]);
@@ -167,7 +168,7 @@ __device__ __forceinline__ void reduce_finish(double (&v)[K], const Fin& f) {
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       double t = 0.0;
-      for (int i = 0; i < kWarps; ++i) t += s[k][i];
+      for (int i = 0; i < nw; ++i) t += s[k][i];
       f.part[blockIdx.x * K + k] = t;
     }
     __threadfence();
@@ -181,7 +182,7 @@ __device__ __forceinline__ void reduce_finish(double (&v)[K], const Fin& f) {
 #pragma unroll
   for (int k = 0; k < K; ++k) {
     double t = 0.0;
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += kThreads) t += __ldcg(&f.part[b * K + k]);
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) t += __ldcg(&f.part[b * K + k]);
     t = warp_sum(t);
     tot[k] = t;
   }
@@ -194,7 +195,7 @@ __device__ __forceinline__ void reduce_finish(double (&v)[K], const Fin& f) {
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       double t = 0.0;
-      for (int i = 0; i < kWarps; ++i) t += s[k][i];
+      for (int i = 0; i < nw; ++i) t += s[k][i];
       tot[k] = t;
     }
     finalize(f, tot[0]);

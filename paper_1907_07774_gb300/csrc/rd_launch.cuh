@@ -2,7 +2,7 @@
 // instantiation per working precision (rd_kern_f32.cu, rd_kern_f64.cu).
 #pragma once
 
-#include "rd_passes.cuh"
+#include "rd_tma.cuh"
 
 namespace rd {
 
@@ -18,6 +18,10 @@ enum KClass {
 // When timing is on, every launch is bracketed by two CUDA events on its
 // stream; prof_begin returns a token for prof_end (-1 when off).
 int prof_begin(int cls, cudaStream_t s);
+// Tensor map for TMA tiles of a strided pass: box {64 B of i2, L along the
+// axis}, 64-byte swizzle.  Cached per (pointer, grid, element size, axis);
+// false if the map cannot be made (the caller then uses the direct kernels).
+bool strided_map(CUtensorMap* out, const void* ptr, const Geom& g, int esz, int axis);
 void prof_end(int token, cudaStream_t s);
 
 template <typename T>

@@ -74,10 +74,74 @@ cudaError_t launch_pencil(K kern, size_t smem, long long groups_needed, const A&
 
 }  // namespace detail
 
+namespace detail {
+template <typename T>
+inline bool tma_fits(const Geom& g) {
+  const int W = 64 / int(sizeof(T));
+  return g.n[2] % W == 0;
+}
+inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
+template <typename K, typename A>
+cudaError_t launch_tma(K kern, size_t smem, int threads, long long tiles, const A& a, cudaStream_t s, int cls) {
+  const void* fn = reinterpret_cast<const void*>(kern);
+  static std::mutex mu;
+  static std::unordered_map<const void*, int> cache;
+  int cap;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find(fn);
+    if (it == cache.end()) {
+      cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      int occ = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, smem) != cudaSuccess || occ < 1) occ = 1;
+      cap = occ * sm_count();
+      if (cap > kMaxBlocks) cap = kMaxBlocks;
+      cache[fn] = cap;
+    } else {
+      cap = it->second;
+    }
+  }
+  const int grid = (int)(tiles < cap ? tiles : cap);
+  const int tok = prof_begin(cls, s);
+  kern<<<grid, threads, smem, s>>>(a);
+  cudaError_t e = cudaGetLastError();
+  prof_end(tok, s);
+  return e;
+}
+}  // namespace detail
+
 template <typename T>
 cudaError_t Launch<T>::op(int L, const OpArgs<T>& a, cudaStream_t s) {
   using namespace detail;
   const long long npairs = a.g.nn / L / 2;
+  if (a.axis != 2 && a.a_self == 0 && a.acc_in == a.out && a.out && tma_fits<T>(a.g) && aligned16(a.u) &&
+      aligned16(a.kappa) && aligned16(a.out)) {
+    RD_DISPATCH_L(L, {
+      using TS = TmaShape<T, LL>;
+      if constexpr (TS::OK) {
+        OpTmaArgs<T> t;
+        if (strided_map(&t.map_u, a.u, a.g, sizeof(T), a.axis) &&
+            strided_map(&t.map_k, a.kappa, a.g, sizeof(T), a.axis) &&
+            strided_map(&t.map_q, a.out, a.g, sizeof(T), a.axis)) {
+          t.c0 = a.c0;
+          t.use_kf = a.use_kf;
+          t.reduce = a.reduce;
+          t.axis = a.axis;
+          t.g = a.g;
+          t.twA = a.twA;
+          t.twB = a.twB;
+          t.prm = a.prm;
+          t.st = a.fin.st;
+          t.fin = a.fin;
+          const long long tiles = (long long)(a.g.n[2] / TS::W) * (a.axis == 1 ? a.g.n[0] : a.g.n[1]);
+          if (a.axis == 1) return launch_tma(k_op_tma<T, LL, 1>, TS::OP_SMEM, TS::THREADS, tiles, t, s, kcOpStrided);
+          return launch_tma(k_op_tma<T, LL, 0>, TS::OP_SMEM, TS::THREADS, tiles, t, s, kcOpStrided);
+        }
+      }
+      break;
+    })
+  }
   RD_DISPATCH_L(L, {
     constexpr size_t sm = pencil_smem<T, LL>();
     const long long blocks = (npairs + Shape<LL>::G - 1) / Shape<LL>::G;
@@ -90,6 +154,34 @@ template <typename T>
 cudaError_t Launch<T>::dht(int L, int mode, const DhtArgs<T>& a, cudaStream_t s) {
   using namespace detail;
   const long long npairs = a.g.nn / L / 2;
+  if (a.axis != 2 && (mode == kDhtPlain || mode == kDhtSym) && tma_fits<T>(a.g) && aligned16(a.in) &&
+      aligned16(a.out)) {
+    RD_DISPATCH_L(L, {
+      using TS = TmaShape<T, LL>;
+      if constexpr (TS::OK) {
+        DhtTmaArgs<T> t;
+        if (strided_map(&t.map_in, a.in, a.g, sizeof(T), a.axis) &&
+            strided_map(&t.map_out, a.out, a.g, sizeof(T), a.axis)) {
+          t.axis = a.axis;
+          t.g = a.g;
+          t.twA = a.twA;
+          t.twB = a.twB;
+          t.prm = a.prm;
+          t.st = a.st;
+          t.fin = a.fin;
+          const long long tiles = (long long)(a.g.n[2] / TS::W) * (a.axis == 1 ? a.g.n[0] : a.g.n[1]);
+          const int cls = (mode == kDhtSym) ? kcDhtSym : kcDhtPlain;
+          if (mode == kDhtSym) {
+            if (a.axis == 1) return launch_tma(k_dht_tma<T, LL, 1, kDhtSym>, TS::DHT_SMEM, TS::THREADS, tiles, t, s, cls);
+            return launch_tma(k_dht_tma<T, LL, 0, kDhtSym>, TS::DHT_SMEM, TS::THREADS, tiles, t, s, cls);
+          }
+          if (a.axis == 1) return launch_tma(k_dht_tma<T, LL, 1, kDhtPlain>, TS::DHT_SMEM, TS::THREADS, tiles, t, s, cls);
+          return launch_tma(k_dht_tma<T, LL, 0, kDhtPlain>, TS::DHT_SMEM, TS::THREADS, tiles, t, s, cls);
+        }
+      }
+      break;
+    })
+  }
   RD_DISPATCH_L(L, {
     constexpr size_t sm = pencil_smem<T, LL>();
     const long long blocks = (npairs + Shape<LL>::G - 1) / Shape<LL>::G;

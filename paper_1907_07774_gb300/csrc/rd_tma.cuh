@@ -1,0 +1,357 @@
+// TMA-staged pencil passes along the strided axes (0 and 1).
+//
+// A tile is W columns (64 bytes of adjacent i2 values: 16 FP32 or 8 FP64) by
+// the full pencil length L along the pass axis.  cp.async.bulk.tensor moves
+// tiles between global and shared memory with the 64-byte swizzle (16-byte
+// chunk bits [4:5] of the shared-memory byte offset XOR bits [7:8]), which
+// makes the pencil-group reads conflict-free.  The inputs of tile i + 2 are
+// prefetched while tile i is computed (two stages); outputs are written back
+// into their tile in shared memory and stored with a TMA store.  Every
+// mbarrier wait is bounded: on timeout the block records kStTimeout in the
+// solver state and exits together.
+#pragma once
+
+#include <cuda.h>
+
+#include "rd_passes.cuh"
+
+namespace rd {
+
+constexpr int kStTimeout = 7;
+constexpr unsigned kWaitLimit = 1u << 26;   // mbarrier polls before giving up
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+
+// Waits for phase `parity` of the barrier; false after kWaitLimit polls.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+  const uint32_t a = smem_addr(bar);
+  for (unsigned it = 0; it < kWaitLimit; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void fence_barrier_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void tma_load3(void* dst, const CUtensorMap* map, int c0, int c1, int c2, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];" ::"r"(smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_addr(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_store3(const CUtensorMap* map, const void* src, int c0, int c1, int c2) {
+  asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group [%0, {%2, %3, %4}], [%1];" ::"l"(
+                   reinterpret_cast<uint64_t>(map)),
+               "r"(smem_addr(src)), "r"(c0), "r"(c1), "r"(c2)
+               : "memory");
+}
+
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait0() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
+// Tile geometry of the strided-axis TMA kernels.
+template <typename T, int L>
+struct TmaShape {
+  static constexpr int W = 64 / int(sizeof(T));      // columns per tile
+  static constexpr int PAIRS = W / 2;                 // pencil pairs per tile
+  static constexpr int TH = Shape<L>::TH;
+  static constexpr int R = Shape<L>::R;
+  static constexpr int THREADS = PAIRS * TH;
+  static constexpr int TILE_BYTES = 64 * L;           // one field tile
+  static constexpr int XSTRIDE = R * (TH + 1);        // exchange buffer per group (complex)
+  static constexpr int XBYTES = PAIRS * XSTRIDE * int(sizeof(cpx<T>));
+  static constexpr bool OK = THREADS >= 32;           // whole warps only
+  static constexpr size_t OP_SMEM = 5 * size_t(TILE_BYTES) + XBYTES + 1024;
+  static constexpr size_t DHT_SMEM = 2 * size_t(TILE_BYTES) + XBYTES + 1024;
+};
+
+// Pair (columns 2g, 2g + 1) of row `row` inside a swizzled 64-byte-row tile.
+template <typename T>
+__device__ __forceinline__ cpx<T>* tile_pair(unsigned char* tile, int row, int g) {
+  uint32_t b = uint32_t(row) * 64u + uint32_t(g) * uint32_t(2 * sizeof(T));
+  b ^= (b >> 3) & 0x30u;
+  return reinterpret_cast<cpx<T>*>(tile + b);
+}
+
+// Tile t of a strided pass -> TMA coordinates {i2, i1, i0} of its corner.
+__device__ __forceinline__ void tile_coords(const Geom& g, int axis, int W, long long t, int& c0, int& c1,
+                                            int& c2) {
+  const int nb = g.n[2] / W;
+  const int blk = int(t % nb);
+  const int other = int(t / nb);
+  c0 = blk * W;
+  if (axis == 1) {
+    c1 = 0;
+    c2 = other;   // i0
+  } else {
+    c1 = other;   // i1
+    c2 = 0;
+  }
+}
+
+template <typename T>
+struct OpTmaArgs {
+  CUtensorMap map_u;
+  CUtensorMap map_k;
+  CUtensorMap map_q;   // accumulator: loaded, updated and stored in place
+  double c0;
+  int use_kf;
+  int reduce;
+  int axis;
+  Geom g;
+  const cpx<T>* twA;
+  const cpx<T>* twB;
+  Params* prm;
+  PcgState* st;
+  Fin fin;
+};
+
+// q <- q + coef * d_axis(kappa d_axis u), coef = c0 (k_f) s; optional sum(u q).
+template <typename T, int L, int AXIS>
+__global__ void __launch_bounds__(TmaShape<T, L>::THREADS) k_op_tma(const __grid_constant__ OpTmaArgs<T> a) {
+  using S = TmaShape<T, L>;
+  constexpr int R = S::R, TH = S::TH, TB = S::TILE_BYTES;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  unsigned char* u_st[2] = {smem, smem + TB};
+  unsigned char* k_st[2] = {smem + 2 * TB, smem + 3 * TB};
+  unsigned char* q_buf = smem + 4 * TB;
+  cpx<T>* xbuf = reinterpret_cast<cpx<T>*>(smem + 5 * TB);
+  __shared__ uint64_t full[2], qbar;
+  const int g = threadIdx.x / TH, t = threadIdx.x % TH;
+  cpx<T>* sm = xbuf + g * S::XSTRIDE;
+  const long long ntiles = (long long)(a.g.n[2] / S::W) * (AXIS == 1 ? a.g.n[0] : a.g.n[1]);
+  const T coef = T(a.c0 * (a.use_kf ? a.prm->k_f : 1.0) * a.prm->s / (double(L) * double(L)));
+
+  auto issue_uk = [&](long long tile, int b) {
+    int c0, c1, c2;
+    tile_coords(a.g, AXIS, S::W, tile, c0, c1, c2);
+    mbar_expect_tx(&full[b], 2 * TB);
+    tma_load3(u_st[b], &a.map_u, c0, c1, c2, &full[b]);
+    tma_load3(k_st[b], &a.map_k, c0, c1, c2, &full[b]);
+  };
+  auto issue_q = [&](long long tile) {
+    int c0, c1, c2;
+    tile_coords(a.g, AXIS, S::W, tile, c0, c1, c2);
+    mbar_expect_tx(&qbar, TB);
+    tma_load3(q_buf, &a.map_q, c0, c1, c2, &qbar);
+  };
+
+  if (threadIdx.x == 0) {
+    mbar_init(&full[0], 1);
+    mbar_init(&full[1], 1);
+    mbar_init(&qbar, 1);
+    fence_barrier_init();
+  }
+  __syncthreads();
+  const long long t0 = blockIdx.x, stride = gridDim.x;
+  if (threadIdx.x == 0) {
+    if (t0 < ntiles) {
+      issue_uk(t0, 0);
+      issue_q(t0);
+    }
+    if (t0 + stride < ntiles) issue_uk(t0 + stride, 1);
+  }
+  double red = 0.0;
+  bool bad = false;
+  int i = 0;
+  for (long long tile = t0; tile < ntiles; tile += stride, ++i) {
+    const int b = i & 1;
+    bool ok = mbar_wait(&full[b], (i >> 1) & 1);
+    if (__syncthreads_or(!ok)) { bad = true; break; }
+    cpx<T> v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = *tile_pair<T>(u_st[b], idx_a<L>(r, t), g);
+    fft_ab<T, L, -1>(v, sm, t, a.twA);
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = times_ik(v[r], kwave<L>(idx_b<L>(r, t)));
+    fft_ba<T, L, +1>(v, sm, t, a.twB);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      cpx<T> k = *tile_pair<T>(k_st[b], idx_a<L>(r, t), g);
+      v[r].x *= k.x;
+      v[r].y *= k.y;
+    }
+    fft_ab<T, L, -1>(v, sm, t, a.twA);
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = times_ik(v[r], kwave<L>(idx_b<L>(r, t)));
+    fft_ba<T, L, +1>(v, sm, t, a.twB);
+    ok = mbar_wait(&qbar, i & 1);
+    if (__syncthreads_or(!ok)) { bad = true; break; }
+    T loc = T(0);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      cpx<T>* qp = tile_pair<T>(q_buf, idx_a<L>(r, t), g);
+      cpx<T> q = *qp;
+      q.x += coef * v[r].x;
+      q.y += coef * v[r].y;
+      if (a.reduce) {
+        cpx<T> u = *tile_pair<T>(u_st[b], idx_a<L>(r, t), g);
+        loc += u.x * q.x + u.y * q.y;
+      }
+      *qp = q;
+    }
+    red += double(loc);
+    fence_proxy_async();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int c0, c1, c2;
+      tile_coords(a.g, AXIS, S::W, tile, c0, c1, c2);
+      tma_store3(&a.map_q, q_buf, c0, c1, c2);
+      bulk_commit();
+      if (tile + 2 * stride < ntiles) issue_uk(tile + 2 * stride, b);
+      bulk_wait_read0();
+      if (tile + stride < ntiles) issue_q(tile + stride);
+    }
+  }
+  if (threadIdx.x == 0) bulk_wait0();
+  if (bad) {
+    if (threadIdx.x == 0) a.st->status = kStTimeout;
+    return;
+  }
+  if (a.reduce) {
+    double vv[1] = {red};
+    reduce_finish<1>(vv, a.fin);
+  }
+}
+
+template <typename T>
+struct DhtTmaArgs {
+  CUtensorMap map_in;
+  CUtensorMap map_out;
+  int axis;
+  Geom g;
+  const cpx<T>* twA;
+  const cpx<T>* twB;
+  Params* prm;
+  PcgState* st;
+  Fin fin;
+};
+
+// Hartley pass along a strided axis: MODE kDhtPlain (out = H in, written at
+// layout-B positions of each pencil) or kDhtSym (out = H S' H in, rz reduced).
+template <typename T, int L, int AXIS, int MODE>
+__global__ void __launch_bounds__(TmaShape<T, L>::THREADS) k_dht_tma(const __grid_constant__ DhtTmaArgs<T> a) {
+  using S = TmaShape<T, L>;
+  constexpr int R = S::R, TH = S::TH, TB = S::TILE_BYTES;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  unsigned char* st_buf[2] = {smem, smem + TB};
+  cpx<T>* xbuf = reinterpret_cast<cpx<T>*>(smem + 2 * TB);
+  __shared__ uint64_t full[2];
+  const int g = threadIdx.x / TH, t = threadIdx.x % TH;
+  cpx<T>* sm = xbuf + g * S::XSTRIDE;
+  const long long ntiles = (long long)(a.g.n[2] / S::W) * (AXIS == 1 ? a.g.n[0] : a.g.n[1]);
+  double symc = 0.0, inv_nn = 0.0;
+  if (MODE == kDhtSym) {
+    symc = a.prm->s * a.prm->k_f * a.prm->kbar1;
+    inv_nn = a.prm->inv_nn;
+  }
+  auto issue = [&](long long tile, int b) {
+    int c0, c1, c2;
+    tile_coords(a.g, AXIS, S::W, tile, c0, c1, c2);
+    mbar_expect_tx(&full[b], TB);
+    tma_load3(st_buf[b], &a.map_in, c0, c1, c2, &full[b]);
+  };
+  if (threadIdx.x == 0) {
+    mbar_init(&full[0], 1);
+    mbar_init(&full[1], 1);
+    fence_barrier_init();
+  }
+  __syncthreads();
+  const long long t0 = blockIdx.x, stride = gridDim.x;
+  if (threadIdx.x == 0) {
+    if (t0 < ntiles) issue(t0, 0);
+    if (t0 + stride < ntiles) issue(t0 + stride, 1);
+  }
+  double red = 0.0;
+  bool bad = false;
+  int i = 0;
+  for (long long tile = t0; tile < ntiles; tile += stride, ++i) {
+    const int b = i & 1;
+    bool ok = mbar_wait(&full[b], (i >> 1) & 1);
+    if (__syncthreads_or(!ok)) { bad = true; break; }
+    cpx<T> v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = *tile_pair<T>(st_buf[b], idx_a<L>(r, t), g);
+    fft_ab<T, L, -1>(v, sm, t, a.twA);
+    hartley_combine<T, L, true>(v, t);
+    T loc = T(0);
+    if (MODE == kDhtSym) {
+      int c0, c1, c2;
+      tile_coords(a.g, AXIS, S::W, tile, c0, c1, c2);
+      const int i1 = c1, i2 = c0 + 2 * g;
+      const int k1 = kwave_rt(i1, a.g.n[1]), k2a = kwave_rt(i2, a.g.n[2]), k2b = kwave_rt(i2 + 1, a.g.n[2]);
+      const T base_a = T(k1 * k1 + k2a * k2a);
+      const T base_b = T(k1 * k1 + k2b * k2b);
+      const T symcT = T(symc), innT = T(inv_nn);
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int k0 = kwave<L>(idx_b<L>(r, t));
+        const T kk = T(k0 * k0);
+        const T sa = innT * recip(T(1) + symcT * (base_a + kk));
+        const T sb = innT * recip(T(1) + symcT * (base_b + kk));
+        loc += sa * v[r].x * v[r].x + sb * v[r].y * v[r].y;
+        v[r].x *= sa;
+        v[r].y *= sb;
+      }
+      fft_ba<T, L, -1>(v, sm, t, a.twB);
+      hartley_combine<T, L, false>(v, t);
+#pragma unroll
+      for (int r = 0; r < R; ++r) *tile_pair<T>(st_buf[b], idx_a<L>(r, t), g) = v[r];
+    } else {
+      // the input values of this pencil were read before the exchange; the
+      // whole group has passed a __syncwarp since, so writing in place is safe
+#pragma unroll
+      for (int r = 0; r < R; ++r) *tile_pair<T>(st_buf[b], idx_b<L>(r, t), g) = v[r];
+    }
+    red += double(loc);
+    fence_proxy_async();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int c0, c1, c2;
+      tile_coords(a.g, AXIS, S::W, tile, c0, c1, c2);
+      tma_store3(&a.map_out, st_buf[b], c0, c1, c2);
+      bulk_commit();
+      bulk_wait_read0();
+      if (tile + 2 * stride < ntiles) issue(tile + 2 * stride, b);
+    }
+  }
+  if (threadIdx.x == 0) bulk_wait0();
+  if (bad) {
+    if (threadIdx.x == 0) a.st->status = kStTimeout;
+    return;
+  }
+  if (MODE == kDhtSym) {
+    double vv[1] = {red};
+    reduce_finish<1>(vv, a.fin);
+  }
+}
+
+}  // namespace rd

@@ -180,6 +180,24 @@ def test_forward_problem_64_fp64_matches_oracle():
     assert rel(c1m, c_or) <= 2e-4
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_gradient_64_matches_oracle(prec):
+    """64^3 gradient and Hessian-vector product against the oracle (the
+    TMA-staged strided passes run at this size in both precisions)."""
+    prob = synth.calibration_problem(n=64, nt=4, m=3, sigma=TWO_PI / 32)
+    M = oracle_for(prob)
+    c_true, _ = M.forward(prob.p_true, prob.k_f_true, prob.rho_f_true)
+    d = synth.labels(c_true, synth.ellipsoid_mask(prob.n), 17)
+    J_or, g_or, _, _ = M.gradient(prob.p, prob.k_f, prob.rho_f, d)
+    ctx = gpu_for(prob, prec)
+    ctx.rd_set_data(d)
+    J, g = ctx.rd_gradient(prob.p, prob.k_f, prob.rho_f)
+    assert abs(J - J_or) <= TOL[prec] * abs(J_or)
+    assert rel(g, g_or) <= TOL[prec]
+    v = synth.random_directions(1, len(prob.p) + 2, 23)[0]
+    assert rel(ctx.rd_hessvec(prob.p, prob.k_f, prob.rho_f, v), M.hessvec(prob.p, prob.k_f, prob.rho_f, v)) <= TOL[prec]
+
+
 def _calibration_data(prob, ctx):
     c_true = torch.zeros(prob.n, dtype=torch.float64, device="cuda")
     ctx.rd_forward(prob.p_true, prob.k_f_true, prob.rho_f_true, c_true)
