@@ -44,7 +44,7 @@ struct PcgState {
   double rtol2;   // rtol^2
   int it, maxit, done, status;
   int total_it;   // iterations summed over all solves since reset
-  int pad_;
+  int sticky;     // largest status seen since reset
 };
 
 // Per-call scalars (device resident so that captured launches stay valid).
@@ -68,7 +68,8 @@ enum AccSlot {
 enum StatusCode {
   kStOk = 0,
   kStNoConv = 5,
-  kStNonFinite = 6
+  kStNonFinite = 6,
+  kStTimeout = 7     // a bounded device-side wait gave up
 };
 
 enum FinKind {
@@ -90,6 +91,7 @@ struct Fin {
   double* part;            // per-block partials
   unsigned int* counter;   // completion counter (reset by the last block)
   double* target;          // kFinSet destination
+  unsigned long long cond; // graph WHILE-node handle set to "not done" (0: none)
 };
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -111,14 +113,17 @@ __device__ __forceinline__ void finalize(const Fin& f, double tot) {
       st->rz = 0.0;
       st->beta = 0.0;
       st->alpha = 0.0;
+      st->pq = 1.0;
       st->status = isfinite(tot) ? kStOk : kStNonFinite;
       st->done = (tot > 0.0 && isfinite(tot)) ? 0 : 1;
+      if (st->status > st->sticky) st->sticky = st->status;
+      if (f.cond) cudaGraphSetConditional(f.cond, st->done ? 0u : 1u);
       break;
     case kFinRz: {
       double rz_new = tot;
       st->beta = (st->it == 0 || st->rz == 0.0) ? 0.0 : rz_new / st->rz;
       st->rz = rz_new;
-      if (!isfinite(rz_new)) { st->done = 1; st->status = kStNonFinite; }
+      if (!isfinite(rz_new)) { st->done = 1; st->status = kStNonFinite; st->sticky = kStNonFinite; }
       break;
     }
     case kFinPq:
@@ -130,7 +135,9 @@ __device__ __forceinline__ void finalize(const Fin& f, double tot) {
       st->rr = tot;
       st->it += 1;
       st->total_it += 1;
-      if (!isfinite(tot)) {
+      if (st->sticky == kStTimeout) {
+        st->done = 1;
+      } else if (!isfinite(tot)) {
         st->done = 1;
         st->status = kStNonFinite;
       } else if (tot <= st->rtol2 * st->ff) {
@@ -139,6 +146,8 @@ __device__ __forceinline__ void finalize(const Fin& f, double tot) {
         st->done = 1;
         st->status = kStNoConv;
       }
+      if (st->status > st->sticky) st->sticky = st->status;
+      if (f.cond) cudaGraphSetConditional(f.cond, st->done ? 0u : 1u);
       break;
     case kFinSet:
       *f.target = f.scale * tot;

@@ -113,17 +113,38 @@ __device__ __forceinline__ cpx<T> ldtw(const cpx<T>* p) {
   }
 }
 
+// Twiddle load from a shared-memory copy of the table.  The load is
+// volatile so that the compiler re-reads it at each use instead of keeping
+// every twiddle of a persistent loop live in registers.
+template <typename T>
+__device__ __forceinline__ cpx<T> ldtw_shared(const cpx<T>* p) {
+  const uint32_t a = static_cast<uint32_t>(__cvta_generic_to_shared(p));
+  cpx<T> v;
+  if constexpr (sizeof(T) == 4) {
+    asm volatile("ld.volatile.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(a));
+  } else {
+    asm volatile("ld.volatile.shared.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "r"(a));
+  }
+  return v;
+}
+
+template <bool SH, typename T>
+__device__ __forceinline__ cpx<T> ldtw_any(const cpx<T>* p) {
+  if constexpr (SH) return ldtw_shared(p);
+  else return ldtw(p);
+}
+
 // Twiddle tables (host-computed in FP64, stored in global memory per L):
 //   twA[k1 * TH + t]          = exp(-2 pi i t k1 / L)
 //   twB[(m * TH + n2) * TH + j] = exp(+2 pi i n2 (j + TH m) / L)
-template <typename T, int L, int S>
+template <typename T, int L, int S, bool SH = false>
 __device__ __forceinline__ void fft_ab(cpx<T>* v, cpx<T>* sm, int t, const cpx<T>* __restrict__ twA) {
   using Sh = Shape<L>;
   constexpr int R = Sh::R, TH = Sh::TH, PAD = Sh::PAD;
   Dft<T, R, S>::run(v);
 #pragma unroll
   for (int k1 = 1; k1 < R; ++k1) {
-    cpx<T> w = ldtw(&twA[k1 * TH + t]);
+    cpx<T> w = ldtw_any<SH>(&twA[k1 * TH + t]);
     v[k1] = cmul(v[k1], w.x, S < 0 ? w.y : -w.y);
   }
   __syncwarp();
@@ -138,7 +159,7 @@ __device__ __forceinline__ void fft_ab(cpx<T>* v, cpx<T>* sm, int t, const cpx<T
   for (int m = 0; m < R / TH; ++m) Dft<T, TH, S>::run(v + m * TH);
 }
 
-template <typename T, int L, int S>
+template <typename T, int L, int S, bool SH = false>
 __device__ __forceinline__ void fft_ba(cpx<T>* u, cpx<T>* sm, int j, const cpx<T>* __restrict__ twB) {
   using Sh = Shape<L>;
   constexpr int R = Sh::R, TH = Sh::TH, PAD = Sh::PAD;
@@ -149,7 +170,7 @@ __device__ __forceinline__ void fft_ba(cpx<T>* u, cpx<T>* sm, int j, const cpx<T
 #pragma unroll
     for (int n2 = 0; n2 < TH; ++n2) {
       if (n2 == 0) continue;
-      cpx<T> w = ldtw(&twB[(m * TH + n2) * TH + j]);
+      cpx<T> w = ldtw_any<SH>(&twB[(m * TH + n2) * TH + j]);
       u[m * TH + n2] = cmul(u[m * TH + n2], w.x, S > 0 ? w.y : -w.y);
     }
   __syncwarp();

@@ -18,10 +18,13 @@ enum KClass {
 // When timing is on, every launch is bracketed by two CUDA events on its
 // stream; prof_begin returns a token for prof_end (-1 when off).
 int prof_begin(int cls, cudaStream_t s);
+bool prof_active();
 // Tensor map for TMA tiles of a strided pass: box {64 B of i2, L along the
 // axis}, 64-byte swizzle.  Cached per (pointer, grid, element size, axis);
 // false if the map cannot be made (the caller then uses the direct kernels).
 bool strided_map(CUtensorMap* out, const void* ptr, const Geom& g, int esz, int axis);
+// Tensor map over the [n0 n1][n2] row view: box {n2, rows}, no swizzle.
+bool row_map(CUtensorMap* out, const void* ptr, const Geom& g, int esz, int rows);
 void prof_end(int token, cudaStream_t s);
 
 template <typename T>

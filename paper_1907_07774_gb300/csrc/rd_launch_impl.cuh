@@ -154,6 +154,42 @@ template <typename T>
 cudaError_t Launch<T>::dht(int L, int mode, const DhtArgs<T>& a, cudaStream_t s) {
   using namespace detail;
   const long long npairs = a.g.nn / L / 2;
+  if (a.axis == 2 && (mode == kDhtSetup || mode == kDhtUpdate)) {
+    const void* rr = (mode == kDhtSetup) ? (const void*)a.in : (const void*)a.r;
+    const bool al = aligned16(rr) && aligned16(a.out) &&
+                    (mode == kDhtSetup || (aligned16(a.x) && aligned16(a.p) && aligned16(a.q)));
+    if (al) {
+      RD_DISPATCH_L(L, {
+        using TS = TmaRowShape<T, LL>;
+        if constexpr (TS::OK) {
+          const long long rows = a.g.nn / LL;
+          DhtRowTmaArgs<T> t;
+          bool ok = rows % TS::ROWS == 0 && row_map(&t.map_r, rr, a.g, sizeof(T), TS::ROWS) &&
+                    row_map(&t.map_out, a.out, a.g, sizeof(T), TS::ROWS);
+          if (ok && mode == kDhtUpdate)
+            ok = row_map(&t.map_x, a.x, a.g, sizeof(T), TS::ROWS) && row_map(&t.map_p, a.p, a.g, sizeof(T), TS::ROWS) &&
+                 row_map(&t.map_q, a.q, a.g, sizeof(T), TS::ROWS);
+          else if (ok) {
+            t.map_x = t.map_r;
+            t.map_p = t.map_r;
+            t.map_q = t.map_r;
+          }
+          if (ok) {
+            t.g = a.g;
+            t.twA = a.twA;
+            t.twB = a.twB;
+            t.st = a.st;
+            t.fin = a.fin;
+            const long long tiles = rows / TS::ROWS;
+            if (mode == kDhtUpdate)
+              return launch_tma(k_dht_row_tma<T, LL, kDhtUpdate>, TS::UPD_SMEM, TS::THREADS, tiles, t, s, kcDhtUpdate);
+            return launch_tma(k_dht_row_tma<T, LL, kDhtSetup>, TS::SETUP_SMEM, TS::THREADS, tiles, t, s, kcDhtSetup);
+          }
+        }
+        break;
+      })
+    }
+  }
   if (a.axis != 2 && (mode == kDhtPlain || mode == kDhtSym) && tma_fits<T>(a.g) && aligned16(a.in) &&
       aligned16(a.out)) {
     RD_DISPATCH_L(L, {
@@ -205,6 +241,26 @@ template <typename T>
 cudaError_t Launch<T>::pcg_opx(int L, const PcgOpxArgs<T>& a, cudaStream_t s) {
   using namespace detail;
   const long long npairs = a.g.nn / L / 2;
+  if (aligned16(a.w) && aligned16(a.p) && aligned16(a.q) && aligned16(a.kappa)) {
+    RD_DISPATCH_L(L, {
+      using TS = TmaRowShape<T, LL>;
+      if constexpr (TS::OK) {
+        const long long rows = a.g.nn / LL;
+        PcgOpxTmaArgs<T> t;
+        if (rows % TS::ROWS == 0 && row_map(&t.map_w, a.w, a.g, sizeof(T), TS::ROWS) &&
+            row_map(&t.map_k, a.kappa, a.g, sizeof(T), TS::ROWS) && row_map(&t.map_p, a.p, a.g, sizeof(T), TS::ROWS) &&
+            row_map(&t.map_q, a.q, a.g, sizeof(T), TS::ROWS)) {
+          t.g = a.g;
+          t.twA = a.twA;
+          t.twB = a.twB;
+          t.prm = a.prm;
+          t.st = a.st;
+          return launch_tma(k_pcg_opx_tma<T, LL>, TS::OPX_SMEM, TS::THREADS, rows / TS::ROWS, t, s, kcPcgOpx);
+        }
+      }
+      break;
+    })
+  }
   RD_DISPATCH_L(L, {
     constexpr size_t sm = pencil_smem<T, LL>();
     const long long blocks = (npairs + Shape<LL>::G - 1) / Shape<LL>::G;

@@ -17,7 +17,6 @@
 
 namespace rd {
 
-constexpr int kStTimeout = 7;
 constexpr unsigned kWaitLimit = 1u << 26;   // mbarrier polls before giving up
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
@@ -75,6 +74,15 @@ __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.comm
 __device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait0() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
+// Copy the two twiddle tables of length L into shared memory (whole block).
+template <typename T, int L>
+__device__ __forceinline__ void stage_twiddles(cpx<T>* dst, const cpx<T>* twA, const cpx<T>* twB) {
+  for (int i = threadIdx.x; i < L; i += blockDim.x) {
+    dst[i] = ldtw(&twA[i]);
+    dst[L + i] = ldtw(&twB[i]);
+  }
+}
+
 // Tile geometry of the strided-axis TMA kernels.
 template <typename T, int L>
 struct TmaShape {
@@ -87,8 +95,9 @@ struct TmaShape {
   static constexpr int XSTRIDE = R * (TH + 1);        // exchange buffer per group (complex)
   static constexpr int XBYTES = PAIRS * XSTRIDE * int(sizeof(cpx<T>));
   static constexpr bool OK = THREADS >= 32;           // whole warps only
-  static constexpr size_t OP_SMEM = 5 * size_t(TILE_BYTES) + XBYTES + 1024;
-  static constexpr size_t DHT_SMEM = 2 * size_t(TILE_BYTES) + XBYTES + 1024;
+  static constexpr int TWBYTES = 2 * L * int(sizeof(cpx<T>));
+  static constexpr size_t OP_SMEM = 5 * size_t(TILE_BYTES) + XBYTES + TWBYTES + 1024;
+  static constexpr size_t DHT_SMEM = 2 * size_t(TILE_BYTES) + XBYTES + TWBYTES + 1024;
 };
 
 // Pair (columns 2g, 2g + 1) of row `row` inside a swizzled 64-byte-row tile.
@@ -139,10 +148,14 @@ __global__ void __launch_bounds__(TmaShape<T, L>::THREADS) k_op_tma(const __grid
   constexpr int R = S::R, TH = S::TH, TB = S::TILE_BYTES;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  unsigned char* u_st[2] = {smem, smem + TB};
-  unsigned char* k_st[2] = {smem + 2 * TB, smem + 3 * TB};
+  auto u_st = [&](int b) { return smem + b * TB; };
+  auto k_st = [&](int b) { return smem + (2 + b) * TB; };
   unsigned char* q_buf = smem + 4 * TB;
   cpx<T>* xbuf = reinterpret_cast<cpx<T>*>(smem + 5 * TB);
+  cpx<T>* tws = reinterpret_cast<cpx<T>*>(smem + 5 * TB + S::XBYTES);
+  const cpx<T>* twA = tws;
+  const cpx<T>* twB = tws + L;
+  stage_twiddles<T, L>(tws, a.twA, a.twB);
   __shared__ uint64_t full[2], qbar;
   const int g = threadIdx.x / TH, t = threadIdx.x % TH;
   cpx<T>* sm = xbuf + g * S::XSTRIDE;
@@ -153,8 +166,8 @@ __global__ void __launch_bounds__(TmaShape<T, L>::THREADS) k_op_tma(const __grid
     int c0, c1, c2;
     tile_coords(a.g, AXIS, S::W, tile, c0, c1, c2);
     mbar_expect_tx(&full[b], 2 * TB);
-    tma_load3(u_st[b], &a.map_u, c0, c1, c2, &full[b]);
-    tma_load3(k_st[b], &a.map_k, c0, c1, c2, &full[b]);
+    tma_load3(u_st(b), &a.map_u, c0, c1, c2, &full[b]);
+    tma_load3(k_st(b), &a.map_k, c0, c1, c2, &full[b]);
   };
   auto issue_q = [&](long long tile) {
     int c0, c1, c2;
@@ -187,21 +200,21 @@ __global__ void __launch_bounds__(TmaShape<T, L>::THREADS) k_op_tma(const __grid
     if (__syncthreads_or(!ok)) { bad = true; break; }
     cpx<T> v[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = *tile_pair<T>(u_st[b], idx_a<L>(r, t), g);
-    fft_ab<T, L, -1>(v, sm, t, a.twA);
+    for (int r = 0; r < R; ++r) v[r] = *tile_pair<T>(u_st(b), idx_a<L>(r, t), g);
+    fft_ab<T, L, -1, true>(v, sm, t, twA);
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = times_ik(v[r], kwave<L>(idx_b<L>(r, t)));
-    fft_ba<T, L, +1>(v, sm, t, a.twB);
+    fft_ba<T, L, +1, true>(v, sm, t, twB);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-      cpx<T> k = *tile_pair<T>(k_st[b], idx_a<L>(r, t), g);
+      cpx<T> k = *tile_pair<T>(k_st(b), idx_a<L>(r, t), g);
       v[r].x *= k.x;
       v[r].y *= k.y;
     }
-    fft_ab<T, L, -1>(v, sm, t, a.twA);
+    fft_ab<T, L, -1, true>(v, sm, t, twA);
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = times_ik(v[r], kwave<L>(idx_b<L>(r, t)));
-    fft_ba<T, L, +1>(v, sm, t, a.twB);
+    fft_ba<T, L, +1, true>(v, sm, t, twB);
     ok = mbar_wait(&qbar, i & 1);
     if (__syncthreads_or(!ok)) { bad = true; break; }
     T loc = T(0);
@@ -212,7 +225,7 @@ __global__ void __launch_bounds__(TmaShape<T, L>::THREADS) k_op_tma(const __grid
       q.x += coef * v[r].x;
       q.y += coef * v[r].y;
       if (a.reduce) {
-        cpx<T> u = *tile_pair<T>(u_st[b], idx_a<L>(r, t), g);
+        cpx<T> u = *tile_pair<T>(u_st(b), idx_a<L>(r, t), g);
         loc += u.x * q.x + u.y * q.y;
       }
       *qp = q;
@@ -232,7 +245,7 @@ __global__ void __launch_bounds__(TmaShape<T, L>::THREADS) k_op_tma(const __grid
   }
   if (threadIdx.x == 0) bulk_wait0();
   if (bad) {
-    if (threadIdx.x == 0) a.st->status = kStTimeout;
+    if (threadIdx.x == 0) { a.st->status = kStTimeout; a.st->sticky = kStTimeout; }
     return;
   }
   if (a.reduce) {
@@ -262,8 +275,12 @@ __global__ void __launch_bounds__(TmaShape<T, L>::THREADS) k_dht_tma(const __gri
   constexpr int R = S::R, TH = S::TH, TB = S::TILE_BYTES;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  unsigned char* st_buf[2] = {smem, smem + TB};
+  auto st_buf = [&](int b) { return smem + b * TB; };
   cpx<T>* xbuf = reinterpret_cast<cpx<T>*>(smem + 2 * TB);
+  cpx<T>* tws = reinterpret_cast<cpx<T>*>(smem + 2 * TB + S::XBYTES);
+  const cpx<T>* twA = tws;
+  const cpx<T>* twB = tws + L;
+  stage_twiddles<T, L>(tws, a.twA, a.twB);
   __shared__ uint64_t full[2];
   const int g = threadIdx.x / TH, t = threadIdx.x % TH;
   cpx<T>* sm = xbuf + g * S::XSTRIDE;
@@ -277,7 +294,7 @@ __global__ void __launch_bounds__(TmaShape<T, L>::THREADS) k_dht_tma(const __gri
     int c0, c1, c2;
     tile_coords(a.g, AXIS, S::W, tile, c0, c1, c2);
     mbar_expect_tx(&full[b], TB);
-    tma_load3(st_buf[b], &a.map_in, c0, c1, c2, &full[b]);
+    tma_load3(st_buf(b), &a.map_in, c0, c1, c2, &full[b]);
   };
   if (threadIdx.x == 0) {
     mbar_init(&full[0], 1);
@@ -299,8 +316,8 @@ __global__ void __launch_bounds__(TmaShape<T, L>::THREADS) k_dht_tma(const __gri
     if (__syncthreads_or(!ok)) { bad = true; break; }
     cpx<T> v[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = *tile_pair<T>(st_buf[b], idx_a<L>(r, t), g);
-    fft_ab<T, L, -1>(v, sm, t, a.twA);
+    for (int r = 0; r < R; ++r) v[r] = *tile_pair<T>(st_buf(b), idx_a<L>(r, t), g);
+    fft_ab<T, L, -1, true>(v, sm, t, twA);
     hartley_combine<T, L, true>(v, t);
     T loc = T(0);
     if (MODE == kDhtSym) {
@@ -321,15 +338,15 @@ __global__ void __launch_bounds__(TmaShape<T, L>::THREADS) k_dht_tma(const __gri
         v[r].x *= sa;
         v[r].y *= sb;
       }
-      fft_ba<T, L, -1>(v, sm, t, a.twB);
+      fft_ba<T, L, -1, true>(v, sm, t, twB);
       hartley_combine<T, L, false>(v, t);
 #pragma unroll
-      for (int r = 0; r < R; ++r) *tile_pair<T>(st_buf[b], idx_a<L>(r, t), g) = v[r];
+      for (int r = 0; r < R; ++r) *tile_pair<T>(st_buf(b), idx_a<L>(r, t), g) = v[r];
     } else {
       // the input values of this pencil were read before the exchange; the
       // whole group has passed a __syncwarp since, so writing in place is safe
 #pragma unroll
-      for (int r = 0; r < R; ++r) *tile_pair<T>(st_buf[b], idx_b<L>(r, t), g) = v[r];
+      for (int r = 0; r < R; ++r) *tile_pair<T>(st_buf(b), idx_b<L>(r, t), g) = v[r];
     }
     red += double(loc);
     fence_proxy_async();
@@ -337,7 +354,7 @@ __global__ void __launch_bounds__(TmaShape<T, L>::THREADS) k_dht_tma(const __gri
     if (threadIdx.x == 0) {
       int c0, c1, c2;
       tile_coords(a.g, AXIS, S::W, tile, c0, c1, c2);
-      tma_store3(&a.map_out, st_buf[b], c0, c1, c2);
+      tma_store3(&a.map_out, st_buf(b), c0, c1, c2);
       bulk_commit();
       bulk_wait_read0();
       if (tile + 2 * stride < ntiles) issue(tile + 2 * stride, b);
@@ -345,13 +362,298 @@ __global__ void __launch_bounds__(TmaShape<T, L>::THREADS) k_dht_tma(const __gri
   }
   if (threadIdx.x == 0) bulk_wait0();
   if (bad) {
-    if (threadIdx.x == 0) a.st->status = kStTimeout;
+    if (threadIdx.x == 0) { a.st->status = kStTimeout; a.st->sticky = kStTimeout; }
     return;
   }
   if (MODE == kDhtSym) {
     double vv[1] = {red};
     reduce_finish<1>(vv, a.fin);
   }
+}
+
+}  // namespace rd
+
+namespace rd {
+
+// ------------------------------------------------ contiguous axis (axis 2)
+// A tile is ROWS whole x-pencils (rows of the [n0 n1][n2] view) loaded with
+// a 2D tensor map, box {L, ROWS}, no swizzle.  Element (row, i) of a tile
+// sits at byte (row L + i) sizeof(T).
+template <typename T, int L>
+struct TmaRowShape {
+  static constexpr int TH = Shape<L>::TH;
+  static constexpr int R = Shape<L>::R;
+  static constexpr int BASE = (sizeof(T) == 4) ? 4 : 2;
+  static constexpr int PAIRS = (32 / TH > BASE) ? 32 / TH : BASE;
+  static constexpr int ROWS = 2 * PAIRS;
+  static constexpr int THREADS = PAIRS * TH;
+  static constexpr int TILE_BYTES = ROWS * L * int(sizeof(T));
+  static constexpr int XSTRIDE = R * (TH + 1);
+  static constexpr int XBYTES = PAIRS * XSTRIDE * int(sizeof(cpx<T>));
+  static constexpr bool OK = (THREADS >= 32) && (THREADS % 32 == 0);
+  static constexpr int TWBYTES = 2 * L * int(sizeof(cpx<T>));
+  static constexpr size_t OPX_SMEM = 6 * size_t(TILE_BYTES) + XBYTES + TWBYTES + 1024;
+  static constexpr size_t UPD_SMEM = 8 * size_t(TILE_BYTES) + XBYTES + TWBYTES + 1024;
+  static constexpr size_t SETUP_SMEM = 2 * size_t(TILE_BYTES) + XBYTES + TWBYTES + 1024;
+};
+
+template <typename T, int L>
+__device__ __forceinline__ T* row_elem(unsigned char* tile, int row, int i) {
+  return reinterpret_cast<T*>(tile) + row * L + i;
+}
+
+__device__ __forceinline__ void tma_load2(void* dst, const CUtensorMap* map, int c0, int c1, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+      "[%4];" ::"r"(smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(smem_addr(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_store2(const CUtensorMap* map, const void* src, int c0, int c1) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.tile.bulk_group [%0, {%2, %3}], [%1];" ::"l"(
+                   reinterpret_cast<uint64_t>(map)),
+               "r"(smem_addr(src)), "r"(c0), "r"(c1)
+               : "memory");
+}
+
+template <typename T>
+struct PcgOpxTmaArgs {
+  CUtensorMap map_w;
+  CUtensorMap map_k;
+  CUtensorMap map_p;
+  CUtensorMap map_q;
+  Geom g;
+  const cpx<T>* twA;
+  const cpx<T>* twB;
+  Params* prm;
+  PcgState* st;
+};
+
+// z = H_2(w); p = z + beta p; q = p - s k_f d_2(kappa d_2 p)  (fields written
+// at layout-B positions of each pencil).
+template <typename T, int L>
+__global__ void __launch_bounds__(TmaRowShape<T, L>::THREADS) k_pcg_opx_tma(const __grid_constant__ PcgOpxTmaArgs<T> a) {
+  using S = TmaRowShape<T, L>;
+  constexpr int R = S::R, TH = S::TH, TB = S::TILE_BYTES;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  auto w_st = [&](int b) { return smem + b * TB; };
+  auto k_st = [&](int b) { return smem + (2 + b) * TB; };
+  auto p_st = [&](int b) { return smem + (4 + b) * TB; };
+  cpx<T>* xbuf = reinterpret_cast<cpx<T>*>(smem + 6 * TB);
+  cpx<T>* tws = reinterpret_cast<cpx<T>*>(smem + 6 * TB + S::XBYTES);
+  const cpx<T>* twA = tws;
+  const cpx<T>* twB = tws + L;
+  stage_twiddles<T, L>(tws, a.twA, a.twB);
+  __shared__ uint64_t full[2];
+  const int g = threadIdx.x / TH, t = threadIdx.x % TH;
+  cpx<T>* sm = xbuf + g * S::XSTRIDE;
+  const long long ntiles = a.g.nn / L / S::ROWS;
+  const double betad = a.st->beta;
+  const bool use_p = (betad != 0.0);
+  const T beta = T(betad);
+  const T coef = T(-a.prm->s * a.prm->k_f / (double(L) * double(L)));
+  auto issue = [&](long long tile, int b) {
+    const int row0 = int(tile * S::ROWS);
+    mbar_expect_tx(&full[b], (use_p ? 3 : 2) * TB);
+    tma_load2(w_st(b), &a.map_w, 0, row0, &full[b]);
+    tma_load2(k_st(b), &a.map_k, 0, row0, &full[b]);
+    if (use_p) tma_load2(p_st(b), &a.map_p, 0, row0, &full[b]);
+  };
+  if (threadIdx.x == 0) {
+    mbar_init(&full[0], 1);
+    mbar_init(&full[1], 1);
+    fence_barrier_init();
+  }
+  __syncthreads();
+  const long long t0 = blockIdx.x, stride = gridDim.x;
+  if (threadIdx.x == 0) {
+    if (t0 < ntiles) issue(t0, 0);
+    if (t0 + stride < ntiles) issue(t0 + stride, 1);
+  }
+  bool bad = false;
+  int i = 0;
+  const int ra = 2 * g, rb = 2 * g + 1;
+  for (long long tile = t0; tile < ntiles; tile += stride, ++i) {
+    const int b = i & 1;
+    bool ok = mbar_wait(&full[b], (i >> 1) & 1);
+    if (__syncthreads_or(!ok)) { bad = true; break; }
+    cpx<T> v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int n = idx_a<L>(r, t);
+      v[r] = {*row_elem<T, L>(w_st(b), ra, n), *row_elem<T, L>(w_st(b), rb, n)};
+    }
+    fft_ab<T, L, -1, true>(v, sm, t, twA);
+    hartley_combine<T, L, true>(v, t);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int n = idx_b<L>(r, t);
+      T* pa = row_elem<T, L>(p_st(b), ra, n);
+      T* pb = row_elem<T, L>(p_st(b), rb, n);
+      if (use_p) {
+        v[r].x += beta * *pa;
+        v[r].y += beta * *pb;
+      }
+      *pa = v[r].x;
+      *pb = v[r].y;
+    }
+    fft_ba<T, L, -1, true>(v, sm, t, twB);
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = times_ik(v[r], kwave<L>(idx_a<L>(r, t)));
+    fft_ab<T, L, +1, true>(v, sm, t, twA);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int n = idx_b<L>(r, t);
+      v[r].x *= *row_elem<T, L>(k_st(b), ra, n);
+      v[r].y *= *row_elem<T, L>(k_st(b), rb, n);
+    }
+    fft_ba<T, L, -1, true>(v, sm, t, twB);
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = times_ik(v[r], kwave<L>(idx_a<L>(r, t)));
+    fft_ab<T, L, +1, true>(v, sm, t, twA);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int n = idx_b<L>(r, t);
+      *row_elem<T, L>(w_st(b), ra, n) = *row_elem<T, L>(p_st(b), ra, n) + coef * v[r].x;
+      *row_elem<T, L>(w_st(b), rb, n) = *row_elem<T, L>(p_st(b), rb, n) + coef * v[r].y;
+    }
+    fence_proxy_async();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const int row0 = int(tile * S::ROWS);
+      tma_store2(&a.map_p, p_st(b), 0, row0);
+      tma_store2(&a.map_q, w_st(b), 0, row0);
+      bulk_commit();
+      bulk_wait_read0();
+      if (tile + 2 * stride < ntiles) issue(tile + 2 * stride, b);
+    }
+  }
+  if (threadIdx.x == 0) bulk_wait0();
+  if (bad && threadIdx.x == 0) { a.st->status = kStTimeout; a.st->sticky = kStTimeout; }
+}
+
+template <typename T>
+struct DhtRowTmaArgs {
+  CUtensorMap map_x;
+  CUtensorMap map_p;
+  CUtensorMap map_r;
+  CUtensorMap map_q;
+  CUtensorMap map_out;
+  Geom g;
+  const cpx<T>* twA;
+  const cpx<T>* twB;
+  PcgState* st;
+  Fin fin;
+};
+
+// Setup: ff = ||r||^2, out = H_2(r).
+// Update: x += alpha p, r -= alpha q, rr = ||r||^2, out = H_2(r).
+template <typename T, int L, int MODE>
+__global__ void __launch_bounds__(TmaRowShape<T, L>::THREADS) k_dht_row_tma(const __grid_constant__ DhtRowTmaArgs<T> a) {
+  using S = TmaRowShape<T, L>;
+  constexpr int R = S::R, TH = S::TH, TB = S::TILE_BYTES;
+  constexpr int NF = (MODE == kDhtUpdate) ? 4 : 1;   // fields per stage: r (, x, p, q)
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  // stage b: r at smem + (b NF + 0) TB, x at +1, p at +2, q at +3
+  auto fld = [&](int b, int f) { return smem + (b * NF + f) * TB; };
+  cpx<T>* xbuf = reinterpret_cast<cpx<T>*>(smem + 2 * NF * TB);
+  cpx<T>* tws = reinterpret_cast<cpx<T>*>(smem + 2 * NF * TB + S::XBYTES);
+  const cpx<T>* twA = tws;
+  const cpx<T>* twB = tws + L;
+  stage_twiddles<T, L>(tws, a.twA, a.twB);
+  __shared__ uint64_t full[2];
+  const int g = threadIdx.x / TH, t = threadIdx.x % TH;
+  cpx<T>* sm = xbuf + g * S::XSTRIDE;
+  const long long ntiles = a.g.nn / L / S::ROWS;
+  const T alpha = (MODE == kDhtUpdate) ? T(a.st->alpha) : T(0);
+  auto issue = [&](long long tile, int b) {
+    const int row0 = int(tile * S::ROWS);
+    mbar_expect_tx(&full[b], NF * TB);
+    tma_load2(fld(b, 0), &a.map_r, 0, row0, &full[b]);
+    if (MODE == kDhtUpdate) {
+      tma_load2(fld(b, 1), &a.map_x, 0, row0, &full[b]);
+      tma_load2(fld(b, 2), &a.map_p, 0, row0, &full[b]);
+      tma_load2(fld(b, 3), &a.map_q, 0, row0, &full[b]);
+    }
+  };
+  if (threadIdx.x == 0) {
+    mbar_init(&full[0], 1);
+    mbar_init(&full[1], 1);
+    fence_barrier_init();
+  }
+  __syncthreads();
+  const long long t0 = blockIdx.x, stride = gridDim.x;
+  if (threadIdx.x == 0) {
+    if (t0 < ntiles) issue(t0, 0);
+    if (t0 + stride < ntiles) issue(t0 + stride, 1);
+  }
+  bool bad = false;
+  double red = 0.0;
+  int i = 0;
+  const int ra = 2 * g, rb = 2 * g + 1;
+  for (long long tile = t0; tile < ntiles; tile += stride, ++i) {
+    const int b = i & 1;
+    bool ok = mbar_wait(&full[b], (i >> 1) & 1);
+    if (__syncthreads_or(!ok)) { bad = true; break; }
+    cpx<T> v[R];
+    T loc = T(0);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int n = idx_a<L>(r, t);
+      T* r0 = row_elem<T, L>(fld(b, 0), ra, n);
+      T* r1 = row_elem<T, L>(fld(b, 0), rb, n);
+      cpx<T> rv = {*r0, *r1};
+      if (MODE == kDhtUpdate) {
+        T* x0 = row_elem<T, L>(fld(b, 1), ra, n);
+        T* x1 = row_elem<T, L>(fld(b, 1), rb, n);
+        const T p0 = *row_elem<T, L>(fld(b, 2), ra, n), p1 = *row_elem<T, L>(fld(b, 2), rb, n);
+        const T q0 = *row_elem<T, L>(fld(b, 3), ra, n), q1 = *row_elem<T, L>(fld(b, 3), rb, n);
+        *x0 += alpha * p0;
+        *x1 += alpha * p1;
+        rv.x -= alpha * q0;
+        rv.y -= alpha * q1;
+        *r0 = rv.x;
+        *r1 = rv.y;
+      }
+      loc += rv.x * rv.x + rv.y * rv.y;
+      v[r] = rv;
+    }
+    red += double(loc);
+    fft_ab<T, L, -1, true>(v, sm, t, twA);
+    hartley_combine<T, L, true>(v, t);
+    // Hartley values go to the p tile (update) or back into the r tile (setup)
+    unsigned char* ob = (MODE == kDhtUpdate) ? fld(b, 2) : fld(b, 0);
+    if (MODE != kDhtUpdate) __syncwarp();
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int n = idx_b<L>(r, t);
+      *row_elem<T, L>(ob, ra, n) = v[r].x;
+      *row_elem<T, L>(ob, rb, n) = v[r].y;
+    }
+    fence_proxy_async();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const int row0 = int(tile * S::ROWS);
+      if (MODE == kDhtUpdate) {
+        tma_store2(&a.map_x, fld(b, 1), 0, row0);
+        tma_store2(&a.map_r, fld(b, 0), 0, row0);
+      }
+      tma_store2(&a.map_out, ob, 0, row0);
+      bulk_commit();
+      bulk_wait_read0();
+      if (tile + 2 * stride < ntiles) issue(tile + 2 * stride, b);
+    }
+  }
+  if (threadIdx.x == 0) bulk_wait0();
+  if (bad) {
+    if (threadIdx.x == 0) { a.st->status = kStTimeout; a.st->sticky = kStTimeout; }
+    return;
+  }
+  double vv[1] = {red};
+  reduce_finish<1>(vv, a.fin);
 }
 
 }  // namespace rd

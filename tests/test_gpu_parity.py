@@ -154,6 +154,26 @@ def test_checkpoint_recompute_is_bitwise_identical(prec):
     assert np.array_equal(out[1], out[3])
 
 
+def test_graph_and_host_driven_solves_are_bitwise_identical():
+    """PCG solves run as CUDA graphs with a device-side loop once a context
+    is warm; with launch timing on they run host-driven.  Same bits."""
+    prob, M, d = _grad_case(nt=6)
+    ctx = gpu_for(prob, "mixed")
+    ctx.rd_set_data(d)
+    ctx.rd_gradient(prob.p, prob.k_f, prob.rho_f)          # warm: graph built
+    J1, g1 = ctx.rd_gradient(prob.p, prob.k_f, prob.rho_f)
+    it1 = ctx.rd_last_pcg_iters()
+    R.rd_profile_enable(True)
+    try:
+        J2, g2 = ctx.rd_gradient(prob.p, prob.k_f, prob.rho_f)
+        it2 = ctx.rd_last_pcg_iters()
+        prof = R.rd_profile_read()
+    finally:
+        R.rd_profile_enable(False)
+    assert J1 == J2 and np.array_equal(g1, g2) and it1 == it2 > 0
+    assert prof["pcg_opx"][1] == it2
+
+
 def test_beta_p_regularisation_terms():
     prob, M, d = _grad_case()
     M.beta_p = 1e-2
