@@ -22,7 +22,8 @@
  * Conventions
  *   - Grid n[0] x n[1] x n[2], n[2] fastest (C order); point i of an axis of
  *     length n sits at x = 2 pi i / n.  Each n[a] must be one of
- *     8, 16, 32, 64, 128, 256 (RD_ERR_SHAPE otherwise).
+ *     8, 16, 32, 64, 96, 128, 256 (RD_ERR_SHAPE otherwise; 96 = 3 * 32 uses a
+ *     radix-3 stage).
  *   - Every field passed in or out is FP64 and may live in host or device
  *     memory (unified addressing decides); it is only read (or written)
  *     during the call, the library keeps its own copy.
@@ -145,7 +146,8 @@ rd_status rd_apply_precond(rd_ctx* ctx, double k_f, const double* r, double* z);
  * and latency-critical loops that must not pay cudaMalloc's implicit device
  * synchronisation).  Computes z = F^-1 [F r / (1 + coef |k~|^2)] (the PCG
  * preconditioner above with coef = tau/2 k_f mean(kappa1)) for FP64 device
- * fields r and z on grid n[0] x n[1] x n[2] (each 8..256, a power of two;
+ * fields r and z on grid n[0] x n[1] x n[2] (each a power of two from 8 to 256,
+ * or 96;
  * RD_ERR_SHAPE otherwise), ordered on `stream`.  No context, no workspace: the
  * solver scalars, reduction partials and twiddle tables live in one fixed
  * 128 KiB __device__ array of the library, held by every GPU that loads it

@@ -26,7 +26,7 @@
 namespace rd {
 
 bool supported_length(int L) {
-  return L == 8 || L == 16 || L == 32 || L == 64 || L == 128 || L == 256;
+  return L == 8 || L == 16 || L == 32 || L == 64 || L == 96 || L == 128 || L == 256;
 }
 
 // ------------------------------------------------------- launch timing
@@ -164,12 +164,14 @@ void prof_end(int token, cudaStream_t s) {
 namespace {
 
 constexpr double kTwoPi = 6.283185307179586476925286766559;
-constexpr int kNumL = 6;   // 8 .. 256
+constexpr int kNumL = 7;   // 8, 16, 32, 64, 128, 256 and 96
 inline int lidx(int L) {
+  if (L == 96) return 6;
   int i = 0;
   while ((8 << i) < L) ++i;
   return i;
 }
+inline int slot_length(int i) { return i == 6 ? 96 : (8 << i); }
 
 // Bump allocator over the caller's workspace (256-byte alignment).
 struct Carve {
@@ -270,7 +272,7 @@ struct Engine : EngineBase {
     put(e ? (void**)&e->part : &dummy, sizeof(double) * kMaxBlocks * 4);
     put(e ? (void**)&e->counter : &dummy, sizeof(unsigned int) * 64);
     for (int i = 0; i < kNumL; ++i) {
-      const int L = 8 << i;
+      const int L = slot_length(i);
       put(e ? (void**)&e->twA[i] : &dummy, sizeof(cpx<T>) * L);
       put(e ? (void**)&e->twB[i] : &dummy, sizeof(cpx<T>) * L);
     }
@@ -349,8 +351,8 @@ struct Engine : EngineBase {
     // twiddle tables, computed in FP64 on the host
     std::vector<cpx<T>> ta, tb;
     for (int i = 0; i < kNumL; ++i) {
-      const int L = 8 << i;
-      const int R = (L >= 128) ? 16 : (L >= 32 ? 8 : (L >= 8 ? 4 : 2));
+      const int L = slot_length(i);
+      const int R = shape_r(L);
       const int TH = L / R;
       ta.assign(L, cpx<T>{T(0), T(0)});
       tb.assign(L, cpx<T>{T(0), T(0)});

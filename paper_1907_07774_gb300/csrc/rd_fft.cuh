@@ -19,9 +19,14 @@
 
 namespace rd {
 
+// Registers per lane for a pencil of length L (L = R * TH, TH | R, TH | 32).
+__host__ __device__ constexpr int shape_r(int L) {
+  return (L == 96) ? 24 : (L >= 128) ? 16 : (L >= 32 ? 8 : (L >= 8 ? 4 : 2));
+}
+
 template <int L>
 struct Shape {
-  static constexpr int R = (L >= 128) ? 16 : (L >= 32 ? 8 : (L >= 8 ? 4 : 2));
+  static constexpr int R = shape_r(L);
   static constexpr int TH = L / R;       // lanes per pencil
   static constexpr int PAD = TH + 1;     // padded row of the exchange buffer
   static constexpr int GSTRIDE = R * PAD + ((R * PAD) % 16 == 0 ? 8 : 0);
@@ -56,16 +61,52 @@ __device__ __forceinline__ T cos16(int j) {
   }
 }
 
-// x * exp(S * 2 pi i k / M) for a compile-time-resolvable k (M <= 16).
+// cos(2 pi j / 24) for j in 0..23 (exact values of the 24th roots of unity).
+template <typename T>
+__device__ __forceinline__ T cos24(int j) {
+  j = ((j % 24) + 24) % 24;
+  const T c1 = T(0.96592582628906828675), c2 = T(0.86602540378443864676), c3 = T(0.70710678118654752440),
+          c4 = T(0.5), c5 = T(0.25881904510252076235);
+  const int q = (j > 12) ? 24 - j : j;   // cos is even
+  switch (q) {
+    case 0: return T(1);
+    case 1: return c1;
+    case 2: return c2;
+    case 3: return c3;
+    case 4: return c4;
+    case 5: return c5;
+    case 6: return T(0);
+    case 7: return -c5;
+    case 8: return -c4;
+    case 9: return -c3;
+    case 10: return -c2;
+    case 11: return -c1;
+    default: return T(-1);
+  }
+}
+
+// x * exp(S * 2 pi i k / M) for a compile-time-resolvable k; M divides 16
+// or 24.
 template <typename T, int M, int S>
 __device__ __forceinline__ cpx<T> twk(int k, cpx<T> x) {
-  const int j = (k * 16 / M) & 15;
-  if (j == 0) return x;
-  if (j == 4) return {-T(S) * x.y, T(S) * x.x};
-  if (j == 8) return {-x.x, -x.y};
-  if (j == 12) return {T(S) * x.y, -T(S) * x.x};
-  const T c = cos16<T>(j), s = T(S) * cos16<T>(j - 4);
-  return cmul(x, c, s);
+  if constexpr (16 % M == 0) {
+    const int j = (k * 16 / M) & 15;
+    if (j == 0) return x;
+    if (j == 4) return {-T(S) * x.y, T(S) * x.x};
+    if (j == 8) return {-x.x, -x.y};
+    if (j == 12) return {T(S) * x.y, -T(S) * x.x};
+    const T c = cos16<T>(j), s = T(S) * cos16<T>(j - 4);
+    return cmul(x, c, s);
+  } else {
+    static_assert(24 % M == 0, "twiddle denominator must divide 16 or 24");
+    const int j = (k * 24 / M) % 24;
+    if (j == 0) return x;
+    if (j == 6) return {-T(S) * x.y, T(S) * x.x};
+    if (j == 12) return {-x.x, -x.y};
+    if (j == 18) return {T(S) * x.y, -T(S) * x.x};
+    const T c = cos24<T>(j), s = T(S) * cos24<T>(j - 6);
+    return cmul(x, c, s);
+  }
 }
 
 // In-register DFT of M points, natural order in and out, sign S.
@@ -91,6 +132,21 @@ struct Dft {
 template <typename T, int S>
 struct Dft<T, 1, S> {
   __device__ __forceinline__ static void run(cpx<T>*) {}
+};
+// 3-point DFT: X_k = sum_n x_n w^{nk}, w = exp(S 2 pi i / 3) = (-1/2, S sqrt(3)/2).
+template <typename T, int S>
+struct Dft<T, 3, S> {
+  __device__ __forceinline__ static void run(cpx<T>* x) {
+    const T h = T(0.86602540378443864676) * T(S);
+    const cpx<T> a = x[0], b = x[1], c = x[2];
+    const cpx<T> sbc = b + c, dbc = b - c;
+    const cpx<T> m = {a.x - T(0.5) * sbc.x, a.y - T(0.5) * sbc.y};
+    // w b + w^2 c = -1/2 (b + c) + i S sqrt(3)/2 (b - c)
+    const cpx<T> rot = {-h * dbc.y, h * dbc.x};
+    x[0] = a + sbc;
+    x[1] = m + rot;
+    x[2] = m - rot;
+  }
 };
 template <typename T, int S>
 struct Dft<T, 2, S> {

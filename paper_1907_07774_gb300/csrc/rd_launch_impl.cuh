@@ -67,6 +67,7 @@ cudaError_t launch_pencil(K kern, size_t smem, long long groups_needed, const A&
     case 16: { constexpr int LL = 16; __VA_ARGS__ }    \
     case 32: { constexpr int LL = 32; __VA_ARGS__ }    \
     case 64: { constexpr int LL = 64; __VA_ARGS__ }    \
+    case 96: { constexpr int LL = 96; __VA_ARGS__ }    \
     case 128: { constexpr int LL = 128; __VA_ARGS__ }  \
     case 256: { constexpr int LL = 256; __VA_ARGS__ }  \
     default: return cudaErrorInvalidValue;             \

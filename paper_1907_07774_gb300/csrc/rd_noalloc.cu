@@ -26,7 +26,7 @@
 namespace rd {
 namespace {
 
-constexpr int kNumLengths = 6;   // pencil lengths 8, 16, ..., 256
+constexpr int kNumLengths = 7;   // pencil lengths 8, 16, ..., 256 and 96
 constexpr int kMaxLength = 256;
 constexpr int kMaxDevices = 64;
 
@@ -39,7 +39,7 @@ struct StaticScratch {
   cpx<double> twB[kNumLengths][kMaxLength];
 };
 
-constexpr size_t kScratchBytes = 128 * 1024;
+constexpr size_t kScratchBytes = 128 * 1024;   // fits StaticScratch (about 100 KiB)
 static_assert(sizeof(StaticScratch) <= kScratchBytes, "static scratch too small");
 
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
@@ -52,10 +52,12 @@ std::mutex g_mu;
 DeviceSlot g_slots[kMaxDevices];
 
 int length_index(int L) {
+  if (L == 96) return 6;
   int i = 0;
   while ((8 << i) < L) ++i;
   return i;
 }
+int slot_length(int i) { return i == 6 ? 96 : (8 << i); }
 
 // Once per device, with that device current: find the array's device
 // address (the host-side symbol is only a stand-in) and upload the twiddle
@@ -76,8 +78,8 @@ rd_status setup_device(int dev, StaticScratch** out) {
   const double two_pi = 6.283185307179586476925286766559;
   std::vector<cpx<double>> ta(kMaxLength), tb(kMaxLength);
   for (int i = 0; i < kNumLengths; ++i) {
-    const int L = 8 << i;
-    const int R = (L >= 128) ? 16 : (L >= 32 ? 8 : 4);
+    const int L = slot_length(i);
+    const int R = shape_r(L);
     const int TH = L / R;
     for (auto& v : ta) v = {0.0, 0.0};
     for (auto& v : tb) v = {0.0, 0.0};

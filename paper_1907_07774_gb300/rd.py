@@ -165,6 +165,10 @@ class Context:
             self._check(L.rd_create(ctypes.byref(h), ctypes.byref(cfg), self.np, ctypes.c_void_p(aligned),
                                     nbytes.value, ctypes.c_void_p(self.stream.cuda_stream)), None)
         self.h = h
+        self.last_theta = None   # parameters of the trajectory the library holds
+
+    def _remember(self, p, k_f, rho_f):
+        self.last_theta = (np.array(p, dtype=np.float64).reshape(-1), float(k_f), float(rho_f))
 
     def _check(self, status, h):
         if status not in (RD_OK,):
@@ -205,8 +209,10 @@ class Context:
         out = 0
         if c1_out is not None:
             out, keep = _ptr(c1_out)
+        self.last_theta = None
         self._call(lib().rd_forward(self.h, pv.ctypes.data, float(k_f), float(rho_f), out, ctypes.byref(J)),
                    allow_noconv)
+        self._remember(pv, k_f, rho_f)
         return J.value
 
     def rd_adjoint(self, alpha0_out=None, allow_noconv=False):
@@ -223,16 +229,20 @@ class Context:
         pv = _host_vec(p, self.np)
         J = ctypes.c_double(0.0)
         g = np.zeros(self.np + 2)
+        self.last_theta = None
         self._call(lib().rd_gradient(self.h, pv.ctypes.data, float(k_f), float(rho_f), ctypes.byref(J),
                                      g.ctypes.data), allow_noconv)
+        self._remember(pv, k_f, rho_f)
         return J.value, g
 
     def rd_hessvec(self, p, k_f, rho_f, v, allow_noconv=False):
         pv = _host_vec(p, self.np)
         vv = _host_vec(v, self.np + 2)
         hv = np.zeros(self.np + 2)
+        self.last_theta = None
         self._call(lib().rd_hessvec(self.h, pv.ctypes.data, float(k_f), float(rho_f), vv.ctypes.data,
                                     hv.ctypes.data), allow_noconv)
+        self._remember(pv, k_f, rho_f)
         return hv
 
     def rd_apply_operator(self, k_f, u, out):

@@ -52,7 +52,7 @@ def gpu_for(prob, prec, **kw):
 
 # --------------------------------------------------------------- kernels
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-@pytest.mark.parametrize("n", [(16, 32, 64), (256, 8, 16), (8, 128, 8)])
+@pytest.mark.parametrize("n", [(16, 32, 64), (256, 8, 16), (8, 128, 8), (96, 16, 32), (16, 96, 96)])
 def test_operator_single_mode_closed_form(prec, n):
     x0, x1, x2 = coords(n)
     k = (1, 2, 3)
@@ -71,7 +71,7 @@ def test_operator_single_mode_closed_form(prec, n):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-@pytest.mark.parametrize("n", [(16, 16, 16), (8, 16, 32), (32, 32, 32)])
+@pytest.mark.parametrize("n", [(16, 16, 16), (8, 16, 32), (32, 32, 32), (96, 8, 32), (16, 96, 96)])
 def test_operator_and_preconditioner_match_oracle(prec, n):
     prob = small_problem(n, 4)
     M = oracle_for(prob)
@@ -90,7 +90,7 @@ def test_operator_and_preconditioner_match_oracle(prec, n):
 
 # ---------------------------------------------------------------- solves
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-@pytest.mark.parametrize("n,nt", [((16, 16, 16), 4), ((8, 16, 32), 3), ((8, 8, 8), 2)])
+@pytest.mark.parametrize("n,nt", [((16, 16, 16), 4), ((8, 16, 32), 3), ((8, 8, 8), 2), ((32, 96, 16), 3)])
 def test_forward_matches_oracle(prec, n, nt):
     prob = small_problem(n, nt)
     M = oracle_for(prob)
@@ -114,8 +114,9 @@ def _grad_case(n=(16, 16, 16), nt=4):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-def test_gradient_matches_oracle(prec):
-    prob, M, d = _grad_case()
+@pytest.mark.parametrize("n", [(16, 16, 16), (96, 16, 32)])
+def test_gradient_matches_oracle(prec, n):
+    prob, M, d = _grad_case(n=n)
     J_or, g_or, _, a0_or = M.gradient(prob.p, prob.k_f, prob.rho_f, d)
     ctx = gpu_for(prob, prec)
     ctx.rd_set_data(d)
@@ -265,3 +266,43 @@ def test_gradient_256_mixed_against_fp64_and_hessian_symmetry():
     hv = mix.rd_hessvec(prob.p, prob.k_f, prob.rho_f, v)
     hw = mix.rd_hessvec(prob.p, prob.k_f, prob.rho_f, w)
     assert abs(v @ hw - w @ hv) <= 1e-3 * abs(v @ hw)
+
+
+# ------------------------------------------- autograd and Gauss-Newton loop
+def test_autograd_function_backward_is_the_adjoint_gradient():
+    from paper_1907_07774_gb300.autograd import misfit
+
+    prob, M, d = _grad_case()
+    J_or, g_or, _, _ = M.gradient(prob.p, prob.k_f, prob.rho_f, d)
+    ctx = gpu_for(prob, "fp64")
+    ctx.rd_set_data(d)
+    p = torch.tensor(prob.p, dtype=torch.float64, device="cuda", requires_grad=True)
+    kf = torch.tensor(prob.k_f, dtype=torch.float64, requires_grad=True)
+    rf = torch.tensor(prob.rho_f, dtype=torch.float64, requires_grad=True)
+    J = misfit(p, kf, rf, ctx)
+    (2.0 * J).backward()
+    g = np.concatenate([p.grad.cpu().numpy(), [kf.grad.item(), rf.grad.item()]])
+    assert abs(J.item() - J_or) <= 1e-10 * J_or
+    assert rel(g, 2.0 * g_or) <= 1e-10
+    # another solve between forward and backward does not change the result
+    J2 = misfit(p.detach().requires_grad_(True), kf, rf, ctx)
+    ctx.rd_forward(prob.p_true, prob.k_f_true, prob.rho_f_true)
+    kf.grad = None
+    J2.backward()
+    assert abs(kf.grad.item() - g_or[-2]) <= 1e-10 * abs(g_or[-2])
+
+
+def test_gauss_newton_reduces_misfit_on_gpu():
+    from paper_1907_07774_gb300 import gn
+
+    prob = synth.calibration_problem(n=32, nt=8, m=3, sigma=TWO_PI / 16)
+    ctx = gpu_for(prob, "mixed", beta_p=1e-4)
+    c_true = torch.zeros(prob.n, dtype=torch.float64, device="cuda")
+    ctx.rd_forward(prob.p_true, prob.k_f_true, prob.rho_f_true, c_true)
+    ctx.rd_set_data(c_true)           # noise-free data: truth is a minimiser
+    th0 = np.concatenate([prob.p, [prob.k_f, prob.rho_f]])
+    J0, g0 = ctx.rd_gradient(prob.p, prob.k_f, prob.rho_f)
+    res = gn.gauss_newton(ctx, th0, iters=4, cg_maxit=10)
+    Js = [h["misfit"] for h in res.history]
+    assert len(Js) >= 2 and Js[0] < J0 and all(b <= a for a, b in zip(Js, Js[1:]))
+    assert Js[-1] < 0.5 * J0
