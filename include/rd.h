@@ -132,6 +132,21 @@ rd_status rd_last_gradient(const rd_ctx* ctx, double* grad);
 rd_status rd_hessvec(rd_ctx* ctx, const double* p, double k_f, double rho_f, const double* v,
                      double* Hv);
 
+/* Reduced gradients of `count` independent problems -- each its own
+ * context, grid size (uneven sizes allowed), coefficients and data -- in ONE
+ * CUDA-graph launch (config "batched forward + adjoint": many parameter sets
+ * or subjects at once).  The graph has one branch per context; inside a
+ * branch every PCG solve is a device-side WHILE node, so the batch runs with
+ * no host round trip.  p[i] (host, np_i values), k_f[i], rho_f[i] are the
+ * parameters of problem i; misfit[i] (may be NULL) and grad[i] (host, np_i
+ * + 2 values) receive what rd_gradient would return.  The first call for a
+ * list of contexts runs one ordinary gradient on every context that has not
+ * run yet, then captures the graph; later calls with the same list (same
+ * order) replay it with the new parameters.  Contexts may not repeat.
+ * Synchronises every context's stream before and the batch after. */
+rd_status rd_batch_gradient(rd_ctx* const* ctxs, int count, const double* const* p, const double* k_f,
+                            const double* rho_f, double* misfit, double* const* grad);
+
 /* Building blocks, exposed for testing and for callers composing their own
  * solvers.  Au = k_f div(kappa1 grad u) with the Fourier pseudo-spectral
  * derivatives of Sec. 3.3 (i k zeroed at the Nyquist index); z = M^-1 r with
@@ -161,6 +176,10 @@ rd_status rd_apply_precond_static(const int n[3], double coef, const double* r, 
  * the number of solves. */
 int rd_last_pcg_iters(const rd_ctx* ctx);
 int rd_last_pcg_solves(const rd_ctx* ctx);
+/* Of those solves, how many ran as a CUDA graph (device-side iteration loop)
+ * rather than host-driven; host-driven solves are the first two of a
+ * context and every solve while launch timing is on. */
+int rd_last_graph_solves(const rd_ctx* ctx);
 
 /* Optional launch timing, process wide.  rd_profile_enable(1) clears the
  * totals and brackets every kernel launch with two CUDA events on its stream;

@@ -210,7 +210,8 @@ struct EngineBase {
   long long nn = 0;
   cudaStream_t stream = nullptr;
   char err[512] = {0};
-  int last_iters = 0, last_solves = 0;
+  int last_iters = 0, last_solves = 0, last_graph_solves = 0;
+  bool capturing = false;   // enqueue into a stream capture (batch graph)
   bool have_tissue = false, have_basis = false, have_data = false;
   bool have_traj = false, have_grad = false;
   double theta_kf = 0, theta_rho = 0;
@@ -225,6 +226,10 @@ struct EngineBase {
   virtual rd_status hessvec(const double*, double, double, const double*, double*) = 0;
   virtual rd_status apply_operator(double, const double*, double*) = 0;
   virtual rd_status apply_precond(double, const double*, double*) = 0;
+  virtual rd_status batch_enqueue(const double*, double, double, cudaStream_t) = 0;
+  virtual rd_status batch_finish(double*, double*) = 0;
+  virtual void batch_prepare(const double*, double, double) = 0;
+  virtual bool warm() const = 0;
 };
 
 template <typename T>
@@ -257,6 +262,11 @@ struct Engine : EngineBase {
   cudaGraphExec_t pcg_exec = nullptr;
   bool graph_failed = false;
   int host_solves = 0;
+  cudaStream_t cap_stream = nullptr;    // internal stream used only for capture
+  cudaStream_t body_stream = nullptr;   // captures WHILE bodies during a batch capture
+  double* hp = nullptr;                 // pinned host copy of p (or v)
+  double* hgp = nullptr;                // pinned host copy of g_p
+  double* hv = nullptr;                 // pinned host copy of a direction v
 
   // ------------------------------------------------------------ set-up
   static size_t layout(Carve& c, const rd_config& cfg, int np, Engine* e) {
@@ -335,6 +345,13 @@ struct Engine : EngineBase {
     cudaError_t e;
     if ((e = cudaMallocHost(&hprm, sizeof(Params))) != cudaSuccess) return cuda_fail(e, "cudaMallocHost");
     if ((e = cudaMallocHost(&hst, sizeof(PcgState))) != cudaSuccess) return cuda_fail(e, "cudaMallocHost");
+    if ((e = cudaMallocHost(&hp, sizeof(double) * (np + 2))) != cudaSuccess) return cuda_fail(e, "cudaMallocHost");
+    if ((e = cudaMallocHost(&hgp, sizeof(double) * (np + 2))) != cudaSuccess) return cuda_fail(e, "cudaMallocHost");
+    if ((e = cudaMallocHost(&hv, sizeof(double) * (np + 2))) != cudaSuccess) return cuda_fail(e, "cudaMallocHost");
+    if ((e = cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
+      return cuda_fail(e, "cudaStreamCreate");
+    if ((e = cudaStreamCreateWithFlags(&body_stream, cudaStreamNonBlocking)) != cudaSuccess)
+      return cuda_fail(e, "cudaStreamCreate");
     memset(hprm, 0, sizeof(Params));
     memset(hst, 0, sizeof(PcgState));
     hprm->s = 0.5 * cfg.t_end / cfg.nt;
@@ -382,6 +399,11 @@ struct Engine : EngineBase {
     if (pcg_graph) cudaGraphDestroy(pcg_graph);
     if (hprm) cudaFreeHost(hprm);
     if (hst) cudaFreeHost(hst);
+    if (hp) cudaFreeHost(hp);
+    if (hgp) cudaFreeHost(hgp);
+    if (hv) cudaFreeHost(hv);
+    if (cap_stream) cudaStreamDestroy(cap_stream);
+    if (body_stream) cudaStreamDestroy(body_stream);
     if (own_ws && ws) cudaFree(ws);
   }
 
@@ -532,6 +554,17 @@ struct Engine : EngineBase {
 
   // Capture setup + WHILE(iteration) into one executable graph.
   bool build_pcg_graph() {
+    // capture on an internal stream (the caller's stream may be the legacy
+    // default stream, which cannot be captured); the graph is launched on
+    // the caller's stream
+    cudaStream_t user = stream;
+    stream = cap_stream;
+    bool ok = build_pcg_graph_on_stream();
+    stream = user;
+    return ok;
+  }
+
+  bool build_pcg_graph_on_stream() {
     cudaGraph_t gph = nullptr, body = nullptr, cap = nullptr;
     cudaGraphExec_t exec = nullptr;
     cudaGraphConditionalHandle h = 0;
@@ -586,6 +619,46 @@ struct Engine : EngineBase {
     return true;
   }
 
+  // Inside a stream capture: setup on the capturing stream, then a WHILE
+  // node whose body (captured on body_stream) is one PCG iteration.
+  rd_status pcg_captured() {
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t cg = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    cudaError_t e;
+    if ((e = cudaStreamGetCaptureInfo(stream, &cs, nullptr, &cg, &deps, nullptr, &nd)) != cudaSuccess ||
+        cs != cudaStreamCaptureStatusActive)
+      return cuda_fail(e == cudaSuccess ? cudaErrorStreamCaptureInvalidated : e, "capture info");
+    cudaGraphConditionalHandle h = 0;
+    if ((e = cudaGraphConditionalHandleCreate(&h, cg, 1, cudaGraphCondAssignDefault)) != cudaSuccess)
+      return cuda_fail(e, "conditional handle");
+    if ((e = enqueue_setup(h)) != cudaSuccess) return cuda_fail(e, "pcg setup");
+    if ((e = cudaStreamGetCaptureInfo(stream, &cs, nullptr, &cg, &deps, nullptr, &nd)) != cudaSuccess)
+      return cuda_fail(e, "capture info");
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t cn = nullptr;
+    if ((e = cudaGraphAddNode(&cn, cg, deps, nullptr, nd, &cp)) != cudaSuccess) return cuda_fail(e, "while node");
+    if ((e = cudaStreamUpdateCaptureDependencies(stream, &cn, nullptr, 1, cudaStreamSetCaptureDependencies)) !=
+        cudaSuccess)
+      return cuda_fail(e, "capture dependencies");
+    cudaGraph_t body = cp.conditional.phGraph_out[0], junk = nullptr;
+    cudaStream_t outer = stream;
+    stream = body_stream;
+    e = cudaStreamBeginCaptureToGraph(stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+    cudaError_t e2 = (e == cudaSuccess) ? enqueue_iteration(h) : e;
+    cudaError_t e3 = cudaStreamEndCapture(stream, &junk);
+    stream = outer;
+    if (e != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess)
+      return cuda_fail(e != cudaSuccess ? e : (e2 != cudaSuccess ? e2 : e3), "while body");
+    ++last_graph_solves;
+    return RD_OK;
+  }
+
   // Preconditioned CG on (I - s k_f A1) x = f with x0 = 0; f in F_R on entry;
   // the solution is left in F_X and the final residual in F_R.  After two
   // host-driven solves (which also warm every launcher's caches) the solve
@@ -593,11 +666,13 @@ struct Engine : EngineBase {
   rd_status pcg() {
     cudaError_t e;
     ++last_solves;
+    if (capturing) return pcg_captured();
     const bool profiling = prof_active();
     if (!profiling && !graph_failed && host_solves >= 2) {
       if (!pcg_exec && !build_pcg_graph()) graph_failed = true;
       if (pcg_exec) {
         if ((e = cudaGraphLaunch(pcg_exec, stream)) != cudaSuccess) return cuda_fail(e, "pcg graph launch");
+        ++last_graph_solves;
         return RD_OK;
       }
     }
@@ -691,8 +766,9 @@ struct Engine : EngineBase {
     hprm->rho_f = rho_f;
     hprm->v_k = hprm->v_rho = 0.0;
     for (double& x : hprm->acc) x = 0.0;
+    if (p != hp) memcpy(hp, p, sizeof(double) * np);
     if ((e = upload_params()) != cudaSuccess) return cuda_fail(e, "upload params");
-    if ((e = cudaMemcpyAsync(pdev, p, sizeof(double) * np, cudaMemcpyHostToDevice, stream)) != cudaSuccess)
+    if ((e = cudaMemcpyAsync(pdev, hp, sizeof(double) * np, cudaMemcpyHostToDevice, stream)) != cudaSuccess)
       return cuda_fail(e, "upload p");
     PhiArgs<T> pa{};
     pa.fac = fac;
@@ -708,11 +784,25 @@ struct Engine : EngineBase {
       if ((rs = fwd_step(n)) != RD_OK) return rs;
     }
     seg_loaded = stride ? (cfg.nt - 1) / stride : -1;
-    theta_p.assign(p, p + np);
+    theta_p.assign(hp, hp + np);
     theta_kf = k_f;
     theta_rho = rho_f;
     have_traj = true;
     have_grad = false;
+    return RD_OK;
+  }
+
+  // misfit kernel: alpha(1) = d - c(1), acc[misfit], c(1) into F_CS
+  rd_status enqueue_misfit() {
+    cudaError_t e;
+    PwArgs<T> a = pw_args();
+    a.a = css_slot(cfg.nt - 1);
+    a.d = f[F_D];
+    a.out0 = f[F_ALPHA];
+    a.out1 = f[F_CS];
+    a.reduce = 1;
+    a.fin = fin(kFinAcc, kAccMisfit, 0.5 * hprm->h3);
+    if ((e = L_::pw(kPwMisfit, a, stream)) != cudaSuccess) return cuda_fail(e, "misfit");
     return RD_OK;
   }
 
@@ -820,17 +910,24 @@ struct Engine : EngineBase {
     return RD_OK;
   }
 
-  rd_status collect(double* out, const double* vp) {
+  cudaError_t enqueue_results() {
     cudaError_t e;
-    std::vector<double> h(np);
-    if ((e = cudaMemcpyAsync(h.data(), gp, sizeof(double) * np, cudaMemcpyDeviceToHost, stream)) != cudaSuccess)
-      return cuda_fail(e, "read g_p");
-    if ((e = cudaMemcpyAsync(hprm, prm, sizeof(Params), cudaMemcpyDeviceToHost, stream)) != cudaSuccess)
-      return cuda_fail(e, "read params");
-    if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_fail(e, "sync");
-    for (int i = 0; i < np; ++i) out[i] = h[i] + cfg.beta_p * vp[i];
+    if ((e = cudaMemcpyAsync(hgp, gp, sizeof(double) * np, cudaMemcpyDeviceToHost, stream)) != cudaSuccess) return e;
+    if ((e = cudaMemcpyAsync(hprm, prm, sizeof(Params), cudaMemcpyDeviceToHost, stream)) != cudaSuccess) return e;
+    return cudaMemcpyAsync(hst, st, sizeof(PcgState), cudaMemcpyDeviceToHost, stream);
+  }
+
+  void read_results(double* out, const double* vp) {
+    for (int i = 0; i < np; ++i) out[i] = hgp[i] + cfg.beta_p * vp[i];
     out[np] = hprm->acc[kAccGk];
     out[np + 1] = hprm->acc[kAccGrho];
+  }
+
+  rd_status collect(double* out, const double* vp) {
+    cudaError_t e;
+    if ((e = enqueue_results()) != cudaSuccess) return cuda_fail(e, "read results");
+    if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_fail(e, "sync");
+    read_results(out, vp);
     return RD_OK;
   }
 
@@ -838,6 +935,7 @@ struct Engine : EngineBase {
     err[0] = 0;
     last_iters = 0;
     last_solves = 0;
+    last_graph_solves = 0;
     nonconv = false;
     // zero the iteration counter and the sticky status (two adjacent ints)
     cudaMemsetAsync(&st->total_it, 0, 2 * sizeof(int), stream);
@@ -936,7 +1034,7 @@ struct Engine : EngineBase {
   rd_status adjoint(double* alpha0_out) override {
     if (!have_traj) return fail(RD_ERR_STATE, "rd_adjoint needs a preceding rd_forward");
     if (!have_data) return fail(RD_ERR_STATE, "rd_set_data is required");
-    const int it0 = last_iters, so0 = last_solves;
+    const int it0 = last_iters, so0 = last_solves, gs0 = last_graph_solves;
     begin_call();
     rd_status s = run_adjoint();
     if (s != RD_OK) return s;
@@ -948,8 +1046,61 @@ struct Engine : EngineBase {
     s = end_call(s);
     last_iters += it0;
     last_solves += so0;
+    last_graph_solves += gs0;
     return s;
   }
+
+  // ---- batched gradient -------------------------------------------------
+  bool warm() const override { return host_solves >= 2; }
+
+  // Enqueue one whole gradient on `s` (which is being captured into the
+  // batch graph): parameters from pinned host memory, forward, misfit,
+  // adjoint, Phi^T, and the results back to pinned host memory.
+  rd_status batch_enqueue(const double* p, double k_f, double rho_f, cudaStream_t s) override {
+    cudaStream_t user = stream;
+    stream = s;
+    capturing = true;
+    begin_call();
+    rd_status rs = run_forward(p, k_f, rho_f);
+    if (rs == RD_OK) rs = enqueue_misfit();
+    if (rs == RD_OK) rs = run_adjoint();
+    if (rs == RD_OK) {
+      cudaError_t e = enqueue_results();
+      if (e != cudaSuccess) rs = cuda_fail(e, "results");
+    }
+    capturing = false;
+    stream = user;
+    return rs;
+  }
+
+  // After the batch graph has run: the same values rd_gradient returns.
+  rd_status batch_finish(double* misfit, double* grad) override {
+    double reg = 0.0;
+    for (int i = 0; i < np; ++i) reg += hp[i] * hp[i];
+    if (misfit) *misfit = hprm->acc[kAccMisfit] + 0.5 * cfg.beta_p * reg;
+    read_results(grad, hp);
+    last_iters = hst->total_it;
+    theta_p.assign(hp, hp + np);
+    have_traj = true;
+    last_grad.assign(grad, grad + np + 2);
+    have_grad = true;
+    if (hst->sticky == kStTimeout) return fail(RD_ERR_CUDA, "a TMA wait timed out");
+    if (hst->sticky == kStNonFinite) return fail(RD_ERR_NONFINITE, "non-finite value in a PCG solve");
+    if (hst->sticky == kStNoConv) return fail(RD_ERR_NOCONV, "a PCG solve reached pcg_maxit");
+    return RD_OK;
+  }
+
+  // Rewrite the pinned inputs that the batch graph's copy nodes read.
+  void batch_prepare(const double* p, double k_f, double rho_f) override {
+    hprm->k_f = k_f;
+    hprm->rho_f = rho_f;
+    hprm->v_k = hprm->v_rho = 0.0;
+    for (double& x : hprm->acc) x = 0.0;
+    memcpy(hp, p, sizeof(double) * np);
+    hprm_theta_kf = k_f;
+    hprm_theta_rho = rho_f;
+  }
+  double hprm_theta_kf = 0, hprm_theta_rho = 0;
 
   rd_status apply_operator(double k_f, const double* u, double* out) override {
     if (!have_tissue) return fail(RD_ERR_STATE, "rd_set_tissue is required");
@@ -1005,7 +1156,8 @@ struct Engine : EngineBase {
     hprm->v_rho = v[np + 1];
     for (double& x : hprm->acc) x = 0.0;
     if ((e = upload_params()) != cudaSuccess) return cuda_fail(e, "upload params");
-    if ((e = cudaMemcpyAsync(pdev, v, sizeof(double) * np, cudaMemcpyHostToDevice, stream)) != cudaSuccess)
+    memcpy(hv, v, sizeof(double) * np);
+    if ((e = cudaMemcpyAsync(pdev, hv, sizeof(double) * np, cudaMemcpyHostToDevice, stream)) != cudaSuccess)
       return cuda_fail(e, "upload v");
     PhiArgs<T> pa{};
     pa.fac = fac;
@@ -1220,13 +1372,125 @@ int rd_profile_read(double* ms, long long* launches, int n) {
 
 const char* rd_profile_class(int i) { return (i >= 0 && i < rd::kcCount) ? rd::kClassNames[i] : ""; }
 
+namespace {
+// The last batch graph: one branch per context, replayed while the list of
+// contexts is unchanged.
+struct BatchGraph {
+  std::vector<rd_ctx*> ctxs;
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t origin = nullptr;
+  std::vector<cudaStream_t> branch;
+  std::vector<cudaEvent_t> events;
+  void clear() {
+    if (exec) cudaGraphExecDestroy(exec);
+    for (auto s : branch) cudaStreamDestroy(s);
+    for (auto e : events) cudaEventDestroy(e);
+    if (origin) cudaStreamDestroy(origin);
+    exec = nullptr;
+    origin = nullptr;
+    branch.clear();
+    events.clear();
+    ctxs.clear();
+  }
+};
+std::mutex g_batch_mu;
+BatchGraph g_batch;
+}  // namespace
+
+rd_status rd_batch_gradient(rd_ctx* const* ctxs, int count, const double* const* p, const double* k_f,
+                            const double* rho_f, double* misfit, double* const* grad) {
+  if (!ctxs || count < 1 || !p || !k_f || !rho_f || !grad) return RD_ERR_ARG;
+  for (int i = 0; i < count; ++i) {
+    if (!ctxs[i] || !p[i] || !grad[i] || !(k_f[i] >= 0) || !std::isfinite(rho_f[i])) return RD_ERR_ARG;
+    rd::EngineBase* e = ctxs[i]->e;
+    if (!e->have_tissue || !e->have_basis || !e->have_data) {
+      snprintf(e->err, sizeof(e->err), "rd_set_tissue, rd_set_basis and rd_set_data are required");
+      return RD_ERR_STATE;
+    }
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == ctxs[i]) return RD_ERR_ARG;
+  }
+  // contexts that have not run yet do one ordinary gradient first (it warms
+  // every launcher and leaves the solver state the batch graph expects)
+  for (int i = 0; i < count; ++i) {
+    rd::EngineBase* e = ctxs[i]->e;
+    if (!e->warm()) {
+      std::vector<double> gtmp(e->np + 2);
+      double J;
+      rd_status s = rd_gradient(ctxs[i], p[i], k_f[i], rho_f[i], &J, gtmp.data());
+      if (s != RD_OK && s != RD_ERR_NOCONV) return s;
+      if (!e->warm()) {
+        s = rd_gradient(ctxs[i], p[i], k_f[i], rho_f[i], &J, gtmp.data());
+        if (s != RD_OK && s != RD_ERR_NOCONV) return s;
+      }
+    }
+    if (cudaStreamSynchronize(e->stream) != cudaSuccess) return RD_ERR_CUDA;
+  }
+  std::lock_guard<std::mutex> lk(g_batch_mu);
+  const bool same = (int)g_batch.ctxs.size() == count && g_batch.exec &&
+                    std::equal(g_batch.ctxs.begin(), g_batch.ctxs.end(), ctxs);
+  for (int i = 0; i < count; ++i) ctxs[i]->e->batch_prepare(p[i], k_f[i], rho_f[i]);
+  if (!same) {
+    g_batch.clear();
+    BatchGraph& b = g_batch;
+    b.ctxs.assign(ctxs, ctxs + count);
+    cudaError_t ce = cudaStreamCreateWithFlags(&b.origin, cudaStreamNonBlocking);
+    b.branch.resize(count, nullptr);
+    b.events.resize(count + 1, nullptr);
+    for (int i = 0; i < count && ce == cudaSuccess; ++i) ce = cudaStreamCreateWithFlags(&b.branch[i], cudaStreamNonBlocking);
+    for (int i = 0; i <= count && ce == cudaSuccess; ++i) ce = cudaEventCreateWithFlags(&b.events[i], cudaEventDisableTiming);
+    if (ce != cudaSuccess) {
+      g_batch.clear();
+      return RD_ERR_CUDA;
+    }
+    cudaGraph_t graph = nullptr;
+    rd_status st = RD_OK;
+    ce = cudaStreamBeginCapture(b.origin, cudaStreamCaptureModeRelaxed);
+    if (ce == cudaSuccess) ce = cudaEventRecord(b.events[count], b.origin);
+    for (int i = 0; i < count && ce == cudaSuccess && st == RD_OK; ++i) {
+      ce = cudaStreamWaitEvent(b.branch[i], b.events[count], 0);
+      if (ce == cudaSuccess) st = ctxs[i]->e->batch_enqueue(p[i], k_f[i], rho_f[i], b.branch[i]);
+      if (ce == cudaSuccess && st == RD_OK) ce = cudaEventRecord(b.events[i], b.branch[i]);
+      if (ce == cudaSuccess && st == RD_OK) ce = cudaStreamWaitEvent(b.origin, b.events[i], 0);
+    }
+    cudaError_t ee = cudaStreamEndCapture(b.origin, &graph);
+    if (ce == cudaSuccess) ce = ee;
+    if (ce == cudaSuccess && st == RD_OK) ce = cudaGraphInstantiate(&b.exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (ce != cudaSuccess || st != RD_OK) {
+      cudaGetLastError();
+      g_batch.clear();
+      if (st == RD_OK) snprintf(ctxs[0]->e->err, sizeof(ctxs[0]->e->err), "batch graph: %s", cudaGetErrorString(ce));
+      return st != RD_OK ? st : RD_ERR_CUDA;
+    }
+    for (int i = 0; i < count; ++i) ctxs[i]->e->batch_prepare(p[i], k_f[i], rho_f[i]);
+  }
+  cudaError_t ce = cudaGraphLaunch(g_batch.exec, g_batch.origin);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(g_batch.origin);
+  if (ce != cudaSuccess) {
+    snprintf(ctxs[0]->e->err, sizeof(ctxs[0]->e->err), "batch launch: %s", cudaGetErrorString(ce));
+    return RD_ERR_CUDA;
+  }
+  rd_status worst = RD_OK;
+  for (int i = 0; i < count; ++i) {
+    rd_status s = ctxs[i]->e->batch_finish(misfit ? &misfit[i] : nullptr, grad[i]);
+    if (s != RD_OK && (worst == RD_OK || worst == RD_ERR_NOCONV)) worst = s;
+  }
+  return worst;
+}
+
 int rd_last_pcg_iters(const rd_ctx* c) { return c ? c->e->last_iters : 0; }
+int rd_last_graph_solves(const rd_ctx* c) { return c ? c->e->last_graph_solves : 0; }
 int rd_last_pcg_solves(const rd_ctx* c) { return c ? c->e->last_solves : 0; }
 
 const char* rd_last_error(const rd_ctx* c) { return c ? c->e->err : "null context"; }
 
 void rd_destroy(rd_ctx* c) {
   if (!c) return;
+  {
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    if (std::find(g_batch.ctxs.begin(), g_batch.ctxs.end(), c) != g_batch.ctxs.end()) g_batch.clear();
+  }
   delete c->e;
   delete c;
 }

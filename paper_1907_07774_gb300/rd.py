@@ -60,6 +60,8 @@ def lib():
         "rd_apply_precond": ([vp, cd, vp, vp], st),
         "rd_last_pcg_iters": ([vp], ci),
         "rd_last_pcg_solves": ([vp], ci),
+        "rd_last_graph_solves": ([vp], ci),
+        "rd_batch_gradient": ([vp, ci, vp, vp, vp, vp, vp], st),
         "rd_last_error": ([vp], ctypes.c_char_p),
         "rd_destroy": ([vp], None),
         "rd_apply_precond_static": ([vp, cd, vp, vp, vp], st),
@@ -258,11 +260,34 @@ class Context:
     def rd_last_pcg_iters(self):
         return lib().rd_last_pcg_iters(self.h)
 
+    def rd_last_graph_solves(self):
+        return lib().rd_last_graph_solves(self.h)
+
     def rd_last_pcg_solves(self):
         return lib().rd_last_pcg_solves(self.h)
 
     def rd_last_error(self):
         return lib().rd_last_error(self.h).decode()
+
+
+def rd_batch_gradient(ctxs, thetas, allow_noconv=False):
+    """Gradients of several contexts in one graph launch.  thetas: list of
+    (p, k_f, rho_f).  Returns (misfits, gradients)."""
+    n = len(ctxs)
+    hs = (ctypes.c_void_p * n)(*[c.h.value for c in ctxs])
+    ps = [_host_vec(t[0], c.np) for c, t in zip(ctxs, thetas)]
+    gs = [np.zeros(c.np + 2) for c in ctxs]
+    pp = (ctypes.c_void_p * n)(*[a.ctypes.data for a in ps])
+    gp = (ctypes.c_void_p * n)(*[a.ctypes.data for a in gs])
+    kf = (ctypes.c_double * n)(*[float(t[1]) for t in thetas])
+    rf = (ctypes.c_double * n)(*[float(t[2]) for t in thetas])
+    J = (ctypes.c_double * n)()
+    status = lib().rd_batch_gradient(hs, n, pp, kf, rf, J, gp)
+    if status != RD_OK and not (status == RD_ERR_NOCONV and allow_noconv):
+        raise RDError(status, ctxs[0].rd_last_error())
+    for c, t in zip(ctxs, thetas):
+        c._remember(t[0], t[1], t[2])
+    return list(J), gs
 
 
 def context_for(prob, prec="fp64", **kw):

@@ -164,6 +164,7 @@ def test_graph_and_host_driven_solves_are_bitwise_identical():
     ctx.rd_gradient(prob.p, prob.k_f, prob.rho_f)          # warm: graph built
     J1, g1 = ctx.rd_gradient(prob.p, prob.k_f, prob.rho_f)
     it1 = ctx.rd_last_pcg_iters()
+    assert ctx.rd_last_graph_solves() == ctx.rd_last_pcg_solves() > 0
     R.rd_profile_enable(True)
     try:
         J2, g2 = ctx.rd_gradient(prob.p, prob.k_f, prob.rho_f)
@@ -306,3 +307,26 @@ def test_gauss_newton_reduces_misfit_on_gpu():
     Js = [h["misfit"] for h in res.history]
     assert len(Js) >= 2 and Js[0] < J0 and all(b <= a for a, b in zip(Js, Js[1:]))
     assert Js[-1] < 0.5 * J0
+
+
+def test_batch_gradient_of_uneven_problems_matches_single_gradients():
+    """One graph launch for several contexts of different grid sizes equals
+    the per-context rd_gradient results, on two calls in a row."""
+    shapes = [((16, 16, 16), 4, "mixed"), ((32, 16, 16), 3, "mixed"), ((96, 16, 32), 2, "mixed"),
+              ((16, 16, 16), 3, "fp64")]
+    ctxs, probs = [], []
+    for i, (n, nt, prec) in enumerate(shapes):
+        prob = small_problem(n, nt, seed=3000 + i)
+        M = oracle_for(prob)
+        c_true, _ = M.forward(prob.p_true, prob.k_f_true, prob.rho_f_true)
+        ctx = gpu_for(prob, prec)
+        ctx.rd_set_data(synth.labels(c_true, synth.ellipsoid_mask(prob.n), i))
+        ctxs.append(ctx)
+        probs.append(prob)
+    for scale in (1.0, 1.3):
+        thetas = [(pr.p * scale, pr.k_f * scale, pr.rho_f / scale) for pr in probs]
+        want = [c.rd_gradient(*t) for c, t in zip(ctxs, thetas)]
+        Js, gs = R.rd_batch_gradient(ctxs, thetas)
+        for (Jw, gw), J, g, c in zip(want, Js, gs, ctxs):
+            assert J == Jw and np.array_equal(g, gw)
+            assert c.rd_last_graph_solves() == c.rd_last_pcg_solves() > 0
