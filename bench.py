@@ -360,6 +360,135 @@ def run_ours(args, rank, world, local):
     return 0
 
 
+def _gpu_setup(local):
+    import torch
+    from paper_1907_07774_gb300 import build as _build
+    _build.build()
+    torch.cuda.set_device(local)
+    return torch
+
+
+def _calibrated_context(R, synth, torch, prob, prec, **kw):
+    ctx = R.context_for(prob, prec=prec, **kw)
+    c_true = torch.zeros(prob.n, dtype=torch.float64, device="cuda")
+    ctx.rd_forward(prob.p_true, prob.k_f_true, prob.rho_f_true, c_true)
+    d = synth.labels(c_true.cpu().numpy(), synth.ellipsoid_mask(prob.n), prob.seed + 7)
+    ctx.rd_set_data(torch.from_numpy(d).cuda())
+    return ctx, d
+
+
+def run_batch(args, rank, world, local):
+    """48 independent problems of uneven size (16 each at 64^3, 96^3, 128^3,
+    nt = 16, mixed), own tissue seeds, k_f ~ U(0.01, 0.1), rho_f ~ U(5, 15),
+    all gradients in one CUDA-graph launch per step."""
+    import numpy as np
+    torch = _gpu_setup(local)
+    from paper_1907_07774_gb300 import rd as R
+    from paper_1907_07774_gb300 import synth
+    rng = np.random.default_rng(3)
+    ctxs, thetas, cells = [], [], 0
+    for i, n in enumerate([64] * 16 + [96] * 16 + [128] * 16):
+        prob = synth.calibration_problem(n=n, nt=16, m=4, seed=3000 + i,
+                                         k_f_true=float(rng.uniform(0.01, 0.1)),
+                                         rho_f_true=float(rng.uniform(5, 15)))
+        ctx, _ = _calibrated_context(R, synth, torch, prob, "mixed", pcg_rtol=1e-6, pcg_maxit=500)
+        ctxs.append(ctx)
+        thetas.append((prob.p, prob.k_f, prob.rho_f))
+        cells += n ** 3 * 16
+    for _ in range(args.warmup):
+        R.rd_batch_gradient(ctxs, thetas)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        Js, gs = R.rd_batch_gradient(ctxs, thetas)
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / args.steps
+    # the same 48 gradients one after another, for comparison
+    t1 = time.perf_counter()
+    for c, t in zip(ctxs, thetas):
+        c.rd_gradient(*t)
+    torch.cuda.synchronize()
+    seq = time.perf_counter() - t1
+    line = {"metric": "batched fwd+adjoint gradient cell-updates/s, 48 uneven instances", "value": cells / dt,
+            "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt,
+            "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "rd_batch_gradient: 16 x 64^3, 16 x 96^3, 16 x 128^3, nt=16, mixed, "
+                                   "one graph launch per step"},
+            "sequential_ms": 1e3 * seq, "batch_speedup_vs_sequential": seq / dt,
+            "misfit_range": [min(Js), max(Js)]}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_newton(args, rank, world, local):
+    """256^3, nt = 32, 125 Gaussians: gradient plus 20 Gauss-Newton
+    Hessian-vector products (the CG of one Newton step), mixed, with the
+    misfit and gradient compared to the FP64 path of the same GPU."""
+    import numpy as np
+    torch = _gpu_setup(local)
+    from paper_1907_07774_gb300 import gn
+    from paper_1907_07774_gb300 import rd as R
+    from paper_1907_07774_gb300 import synth
+    prob = problem(256, 32)
+    ctx, d = _calibrated_context(R, synth, torch, prob, "mixed", pcg_rtol=1e-6, pcg_maxit=500)
+    th = (prob.p, prob.k_f, prob.rho_f)
+    ctx.rd_gradient(*th)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    J, g = ctx.rd_gradient(*th)
+    hv_count = [0]
+
+    def hv(v):
+        hv_count[0] += 1
+        return ctx.rd_hessvec(*th, v)
+    step, used = gn.cg(hv, -g, 20, 1e-12)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    ref = R.context_for(prob, prec="fp64", pcg_rtol=1e-10, pcg_maxit=1000)
+    ref.rd_set_data(torch.from_numpy(d).cuda())
+    J64, g64 = ref.rd_gradient(*th)
+    line = {"metric": "gradient + 20 GN Hessian-vector products at 256^3 (s)", "value": dt, "unit": "s",
+            "higher_is_better": False, "n_gpus": 1, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "256^3 nt=32 np=125 mixed; CG on rd_hessvec, 20 products"},
+            "hessvecs": used, "misfit": J, "misfit_fp64": J64,
+            "misfit_rel_err_vs_fp64": abs(J - J64) / J64,
+            "grad_rel_err_vs_fp64": float(np.linalg.norm(g - g64) / np.linalg.norm(g64)),
+            "newton_step_norm": float(np.linalg.norm(step))}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gn(args, rank, world, local):
+    """Gauss-Newton calibration at 256^3, nt = 64, sqrt(nt) checkpointing,
+    from k_f = 0.02, rho_f = 6 (mixed); reports time per iteration and the
+    recovered-parameter error against the ground truth."""
+    import numpy as np
+    torch = _gpu_setup(local)
+    from paper_1907_07774_gb300 import gn
+    from paper_1907_07774_gb300 import rd as R
+    from paper_1907_07774_gb300 import synth
+    prob = synth.calibration_problem(n=args.n, nt=64, m=5)
+    ctx, d = _calibrated_context(R, synth, torch, prob, "mixed", pcg_rtol=1e-6, pcg_maxit=500, ckpt_stride=8,
+                                 beta_p=1e-4)
+    th0 = np.concatenate([prob.p, [prob.k_f, prob.rho_f]])
+    truth = np.concatenate([prob.p_true, [prob.k_f_true, prob.rho_f_true]])
+    t0 = time.perf_counter()
+    res = gn.gauss_newton(ctx, th0, iters=args.gn_iters, cg_maxit=20)
+    dt = time.perf_counter() - t0
+    its = max(1, len(res.history))
+    err = lambda th: {"p_rel": float(np.linalg.norm(th[:-2] - truth[:-2]) / np.linalg.norm(truth[:-2])),
+                      "k_f_rel": abs(th[-2] - truth[-2]) / truth[-2], "rho_f_rel": abs(th[-1] - truth[-1]) / truth[-1]}
+    line = {"metric": "Gauss-Newton iteration time at 256^3 nt=64 (s)", "value": dt / its, "unit": "s/iteration",
+            "higher_is_better": False, "n_gpus": 1, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{args.n}^3 nt=64 np=125 mixed ckpt_stride=8 beta_p=1e-4, "
+                                   f"{args.gn_iters} GN iterations, CG <= 20 Hessian-vector products"},
+            "iterations": len(res.history), "start_error": err(th0), "final_error": err(res.theta),
+            "misfit_history": [h["misfit"] for h in res.history],
+            "hessvecs": [h["hessvecs"] for h in res.history]}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -371,10 +500,20 @@ def main():
     ap.add_argument("--ckpt-stride", type=int, default=0)
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="gradient", choices=["gradient", "batch", "newton", "gn"],
+                    help="gradient: the headline 256^3 gradient; batch: 48 uneven instances in one graph; "
+                         "newton: gradient + 20 Hessian-vector products; gn: Gauss-Newton calibration")
+    ap.add_argument("--gn-iters", type=int, default=10)
     args = ap.parse_args()
     rank, world, local = env_rank()
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.workload == "batch":
+        return run_batch(args, rank, world, local)
+    if args.workload == "newton":
+        return run_newton(args, rank, world, local)
+    if args.workload == "gn":
+        return run_gn(args, rank, world, local)
     return run_ours(args, rank, world, local)
 
 

@@ -169,7 +169,8 @@ rd_status rd_apply_precond(rd_ctx* ctx, double k_f, const double* r, double* z);
  * until exit.  The first call on a device finds that array's address and
  * uploads the tables (synchronously); make that first call before any stream
  * capture.  All calls share the array, so calls that overlap on the GPU race;
- * order them on one stream.  r is not modified; z may not alias r. */
+ * order them on one stream.  r is not modified; z may not alias r; both
+ * must be 16-byte aligned (RD_ERR_ARG otherwise). */
 rd_status rd_apply_precond_static(const int n[3], double coef, const double* r, double* z, void* stream);
 
 /* Counters of the last call: PCG iterations summed over its solves, and

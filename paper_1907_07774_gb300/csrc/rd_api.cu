@@ -519,6 +519,7 @@ struct Engine : EngineBase {
       a.twB = twB[lidx(g.n[2])];
       a.prm = prm;
       a.st = st;
+      a.fin = fin(kFinPqAdd, 0, 1.0 / (double(g.n[2]) * g.n[2]));
       if ((e = L_::pcg_opx(g.n[2], a, stream)) != cudaSuccess) return e;
     }
     for (int axis : {1, 0}) {
@@ -530,13 +531,13 @@ struct Engine : EngineBase {
       a.c0 = -1.0;
       a.use_kf = 1;
       a.a_self = 0;
-      a.reduce = (axis == 0);
+      a.reduce = 1;
       a.axis = axis;
       a.g = g;
       a.twA = twA[lidx(g.n[axis])];
       a.twB = twB[lidx(g.n[axis])];
       a.prm = prm;
-      a.fin = fin(kFinPq);
+      a.fin = fin(axis == 0 ? kFinPqLast : kFinPqAdd, 0, 1.0 / (double(g.n[axis]) * g.n[axis]));
       if ((e = L_::op(g.n[axis], a, stream)) != cudaSuccess) return e;
     }
     {

@@ -11,8 +11,10 @@ namespace rd {
 constexpr int kThreads = 256;   // threads per block of every field kernel
 constexpr int kWarps = kThreads / 32;
 
+// Complex value; aligned to its full size so that tables and buffers of
+// cpx<double> can be read with 16-byte vector loads.
 template <typename T>
-struct cpx {
+struct alignas(2 * sizeof(T)) cpx {
   T x, y;
 };
 
@@ -40,6 +42,7 @@ struct PcgState {
   double rr;      // ||r||^2
   double rz;      // (r, M^-1 r)
   double pq;      // (p, (I - sA) p)
+  double pq_part; // partial sums of pq from the passes before the last
   double alpha, beta;
   double rtol2;   // rtol^2
   int it, maxit, done, status;
@@ -79,7 +82,9 @@ enum FinKind {
   kFinRz,       // rz update and beta
   kFinPq,       // alpha
   kFinRr,       // residual norm, iteration count, convergence
-  kFinSet       // *target = scale * total
+  kFinSet,      // *target = scale * total
+  kFinPqAdd,    // pq_part += [tot0] + scale s k_f tot_last   (p.p and kappa |d p|^2 terms)
+  kFinPqLast    // pq = pq_part + scale s k_f tot; alpha = rz / pq
 };
 
 struct Fin {
@@ -100,11 +105,18 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-__device__ __forceinline__ void finalize(const Fin& f, double tot) {
+// (p, (I - s A) p) = |p|^2 + s k_f sum_a sum_x kappa1 (d_a p)^2 (the
+// spectral first derivative is antisymmetric), accumulated pass by pass.
+__device__ __forceinline__ double pq_term(const Fin& f, const double* tot, int K) {
+  return (K >= 2 ? tot[0] : 0.0) + tot[K - 1] * f.scale * f.prm->s * f.prm->k_f;
+}
+
+__device__ __forceinline__ void finalize(const Fin& f, const double* tots, int K) {
   PcgState* st = f.st;
+  const double tot = tots[0];
   switch (f.kind) {
     case kFinAcc:
-      f.prm->acc[f.slot] += f.scale * tot;
+      for (int k = 0; k < K; ++k) f.prm->acc[f.slot + k] += f.scale * tots[k];
       break;
     case kFinSetup:
       st->ff = tot;
@@ -114,6 +126,7 @@ __device__ __forceinline__ void finalize(const Fin& f, double tot) {
       st->beta = 0.0;
       st->alpha = 0.0;
       st->pq = 1.0;
+      st->pq_part = 0.0;
       st->status = isfinite(tot) ? kStOk : kStNonFinite;
       st->done = (tot > 0.0 && isfinite(tot)) ? 0 : 1;
       if (st->status > st->sticky) st->sticky = st->status;
@@ -131,6 +144,17 @@ __device__ __forceinline__ void finalize(const Fin& f, double tot) {
       st->alpha = (tot > 0.0) ? st->rz / tot : 0.0;
       if (!isfinite(tot)) { st->done = 1; st->status = kStNonFinite; }
       break;
+    case kFinPqAdd:
+      st->pq_part += pq_term(f, tots, K);
+      break;
+    case kFinPqLast: {
+      const double pq = st->pq_part + pq_term(f, tots, K);
+      st->pq_part = 0.0;
+      st->pq = pq;
+      st->alpha = (pq > 0.0) ? st->rz / pq : 0.0;
+      if (!isfinite(pq)) { st->done = 1; st->status = kStNonFinite; }
+      break;
+    }
     case kFinRr:
       st->rr = tot;
       st->it += 1;
@@ -207,14 +231,7 @@ __device__ __forceinline__ void reduce_finish(double (&v)[K], const Fin& f) {
       for (int i = 0; i < nw; ++i) t += s[k][i];
       tot[k] = t;
     }
-    finalize(f, tot[0]);
-    if (K > 1) {
-      Fin g = f;
-      for (int k = 1; k < K; ++k) {
-        g.slot = f.slot + k;
-        finalize(g, tot[k]);
-      }
-    }
+    finalize(f, tot, K);
     *f.counter = 0u;
   }
 }

@@ -256,6 +256,7 @@ cudaError_t Launch<T>::pcg_opx(int L, const PcgOpxArgs<T>& a, cudaStream_t s) {
           t.twB = a.twB;
           t.prm = a.prm;
           t.st = a.st;
+          t.fin = a.fin;
           return launch_tma(k_pcg_opx_tma<T, LL>, TS::OPX_SMEM, TS::THREADS, rows / TS::ROWS, t, s, kcPcgOpx);
         }
       }

@@ -16,6 +16,7 @@
 // before its kernels run.  Calls that overlap on the GPU (different streams,
 // or different host threads without ordering) race on this array.
 #include <cmath>
+#include <cstddef>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -30,14 +31,18 @@ constexpr int kNumLengths = 7;   // pencil lengths 8, 16, ..., 256 and 96
 constexpr int kMaxLength = 256;
 constexpr int kMaxDevices = 64;
 
+// Every member starts on a 256-byte boundary (the twiddle tables are read
+// with 16-byte vector loads).
 struct StaticScratch {
-  Params prm;
-  PcgState st;
-  unsigned int counter[64];
-  double part[kMaxBlocks];
-  cpx<double> twA[kNumLengths][kMaxLength];
-  cpx<double> twB[kNumLengths][kMaxLength];
+  alignas(256) Params prm;
+  alignas(256) PcgState st;
+  alignas(256) unsigned int counter[64];
+  alignas(256) double part[kMaxBlocks];
+  alignas(256) cpx<double> twA[kNumLengths][kMaxLength];
+  alignas(256) cpx<double> twB[kNumLengths][kMaxLength];
 };
+static_assert(offsetof(StaticScratch, twA) % 256 == 0 && offsetof(StaticScratch, twB) % 256 == 0,
+              "twiddle tables must be 256-byte aligned");
 
 constexpr size_t kScratchBytes = 128 * 1024;   // fits StaticScratch (about 100 KiB)
 static_assert(sizeof(StaticScratch) <= kScratchBytes, "static scratch too small");
@@ -115,6 +120,8 @@ extern "C" rd_status rd_apply_precond_static(const int n[3], double coef, const 
                                              void* stream) {
   using namespace rd;
   if (!n || !r || !z || !(coef >= 0.0)) return RD_ERR_ARG;
+  // the pencil kernels read and write pairs of values with 16-byte accesses
+  if ((reinterpret_cast<uintptr_t>(r) & 15) || (reinterpret_cast<uintptr_t>(z) & 15)) return RD_ERR_ARG;
   for (int a = 0; a < 3; ++a)
     if (!supported_length(n[a]) || n[a] > kMaxLength) return RD_ERR_SHAPE;
   int dev = 0;

@@ -101,10 +101,12 @@ __device__ __forceinline__ int kwave_rt(int i, int n) {
 
 // Two derivatives in a row: v (real pencils packed, layout A) is replaced by
 // L^2 d(kappa d v) with kappa loaded from kap at layout A positions.
+// When kred is given, sum kappa (L d v)^2 over the pencil pair into *kred.
 template <typename T, int L, bool CONTIG>
 __device__ __forceinline__ void second_derivative_a(cpx<T>* v, cpx<T>* sm, int t, const cpx<T>* twA,
                                                     const cpx<T>* twB, const T* __restrict__ kap,
-                                                    long long b0, long long b1, long long st, bool act) {
+                                                    long long b0, long long b1, long long st, bool act,
+                                                    T* kred = nullptr) {
   constexpr int R = Shape<L>::R;
   fft_ab<T, L, -1>(v, sm, t, twA);
 #pragma unroll
@@ -113,6 +115,7 @@ __device__ __forceinline__ void second_derivative_a(cpx<T>* v, cpx<T>* sm, int t
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     cpx<T> k = act ? ld2<T, CONTIG>(kap, b0, b1, (long long)idx_a<L>(r, t) * st) : cpx<T>{T(0), T(0)};
+    if (kred) *kred += k.x * v[r].x * v[r].x + k.y * v[r].y * v[r].y;
     v[r].x *= k.x;
     v[r].y *= k.y;
   }
@@ -124,7 +127,8 @@ __device__ __forceinline__ void second_derivative_a(cpx<T>* v, cpx<T>* sm, int t
 
 // ------------------------------------------------------------ operator pass
 // out = a_self * u + acc_in + coef * d_axis(kappa d_axis u)
-// coef = c0 * (use_kf ? k_f : 1) * s.  Optional reduction of sum(u * out).
+// coef = c0 * (use_kf ? k_f : 1) * s.  Optional reduction of
+// sum kappa (L d_axis u)^2 (the axis's share of (u, (I - sA) u)).
 template <typename T>
 struct OpArgs {
   const T* u;
@@ -162,24 +166,19 @@ __global__ void __launch_bounds__(kThreads) k_op(OpArgs<T> a) {
 #pragma unroll
     for (int r = 0; r < R; ++r)
       v[r] = act ? ld2<T, CONTIG>(a.u, b0, b1, (long long)idx_a<L>(r, t) * st) : cpx<T>{T(0), T(0)};
-    second_derivative_a<T, L, CONTIG>(v, sm, t, a.twA, a.twB, a.kappa, b0, b1, st, act);
+    T kred = T(0);
+    second_derivative_a<T, L, CONTIG>(v, sm, t, a.twA, a.twB, a.kappa, b0, b1, st, act,
+                                      a.reduce ? &kred : nullptr);
+    red += double(kred);
     if (act) {
-      T loc = T(0);
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         const long long off = (long long)idx_a<L>(r, t) * st;
         cpx<T> o = {coef * v[r].x, coef * v[r].y};
-        if (a.a_self || a.reduce) {
-          cpx<T> u = ld2<T, CONTIG>(a.u, b0, b1, off);
-          if (a.a_self) o = o + u;
-          if (a.acc_in) o = o + ld2<T, CONTIG>(a.acc_in, b0, b1, off);
-          if (a.reduce) loc += u.x * o.x + u.y * o.y;
-        } else if (a.acc_in) {
-          o = o + ld2<T, CONTIG>(a.acc_in, b0, b1, off);
-        }
+        if (a.a_self) o = o + ld2<T, CONTIG>(a.u, b0, b1, off);
+        if (a.acc_in) o = o + ld2<T, CONTIG>(a.acc_in, b0, b1, off);
         st2<T, CONTIG>(a.out, b0, b1, off, o);
       }
-      red += double(loc);
     }
   }
   if (a.reduce) {
@@ -317,6 +316,7 @@ struct PcgOpxArgs {
   const cpx<T>* twB;
   Params* prm;
   PcgState* st;
+  Fin fin;   // reduces |p|^2 and sum kappa (L d_2 p)^2 (kFinPqAdd)
 };
 
 template <typename T, int L>
@@ -330,6 +330,7 @@ __global__ void __launch_bounds__(kThreads) k_pcg_opx(PcgOpxArgs<T> a) {
   const double betad = a.st->beta;
   const T beta = T(betad);
   const T coef = T(-a.prm->s * a.prm->k_f / (double(L) * double(L)));
+  double red_pp = 0.0, red_k = 0.0;
   for (long long base = (long long)blockIdx.x * G; base < npairs; base += (long long)gridDim.x * G) {
     const long long pair = base + g;
     const bool act = pair < npairs;
@@ -340,6 +341,7 @@ __global__ void __launch_bounds__(kThreads) k_pcg_opx(PcgOpxArgs<T> a) {
     for (int r = 0; r < R; ++r) v[r] = act ? ld2<T, true>(a.w, b0, b1, idx_a<L>(r, t)) : cpx<T>{T(0), T(0)};
     fft_ab<T, L, -1>(v, sm, t, a.twA);
     hartley_combine<T, L, true>(v, t);
+    T lpp = T(0), lk = T(0);
     if (act) {
 #pragma unroll
       for (int r = 0; r < R; ++r) {
@@ -349,6 +351,7 @@ __global__ void __launch_bounds__(kThreads) k_pcg_opx(PcgOpxArgs<T> a) {
           v[r].x += beta * po.x;
           v[r].y += beta * po.y;
         }
+        lpp += v[r].x * v[r].x + v[r].y * v[r].y;
         st2<T, true>(a.p, b0, b1, off, v[r]);
       }
     }
@@ -360,9 +363,12 @@ __global__ void __launch_bounds__(kThreads) k_pcg_opx(PcgOpxArgs<T> a) {
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       cpx<T> k = act ? ld2<T, true>(a.kappa, b0, b1, idx_b<L>(r, t)) : cpx<T>{T(0), T(0)};
+      lk += k.x * v[r].x * v[r].x + k.y * v[r].y * v[r].y;
       v[r].x *= k.x;
       v[r].y *= k.y;
     }
+    red_pp += double(lpp);
+    red_k += double(lk);
     fft_ba<T, L, -1>(v, sm, t, a.twB);
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = times_ik(v[r], kwave<L>(idx_a<L>(r, t)));
@@ -376,6 +382,8 @@ __global__ void __launch_bounds__(kThreads) k_pcg_opx(PcgOpxArgs<T> a) {
       }
     }
   }
+  double vv[2] = {red_pp, red_k};
+  reduce_finish<2>(vv, a.fin);
 }
 
 // ----------------------------------------------------------- gradient pass

@@ -96,7 +96,7 @@ struct TmaShape {
   static constexpr int XBYTES = PAIRS * XSTRIDE * int(sizeof(cpx<T>));
   static constexpr bool OK = THREADS >= 32;           // whole warps only
   static constexpr int TWBYTES = 2 * L * int(sizeof(cpx<T>));
-  static constexpr size_t OP_SMEM = 5 * size_t(TILE_BYTES) + XBYTES + TWBYTES + 1024;
+  static constexpr size_t OP_SMEM = 3 * size_t(TILE_BYTES) + XBYTES + TWBYTES + 1024;
   static constexpr size_t DHT_SMEM = 2 * size_t(TILE_BYTES) + XBYTES + TWBYTES + 1024;
 };
 
@@ -141,96 +141,97 @@ struct OpTmaArgs {
   Fin fin;
 };
 
-// q <- q + coef * d_axis(kappa d_axis u), coef = c0 (k_f) s; optional sum(u q).
+// q <- q + coef * d_axis(kappa d_axis u), coef = c0 (k_f) s; optionally
+// reduces sum kappa (L d_axis u)^2, this axis's share of (u, (I - sA) u).
+//
+// Shared memory holds one tile each of u, kappa and q plus the FFT exchange
+// area.  Each input of tile i + 1 is requested as soon as this block has
+// taken the corresponding values of tile i into registers (u before the
+// first transform, kappa before the second, q after its store was read), so
+// the loads overlap the transforms while three blocks fit on an SM.
 template <typename T, int L, int AXIS>
 __global__ void __launch_bounds__(TmaShape<T, L>::THREADS) k_op_tma(const __grid_constant__ OpTmaArgs<T> a) {
   using S = TmaShape<T, L>;
   constexpr int R = S::R, TH = S::TH, TB = S::TILE_BYTES;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  auto u_st = [&](int b) { return smem + b * TB; };
-  auto k_st = [&](int b) { return smem + (2 + b) * TB; };
-  unsigned char* q_buf = smem + 4 * TB;
-  cpx<T>* xbuf = reinterpret_cast<cpx<T>*>(smem + 5 * TB);
-  cpx<T>* tws = reinterpret_cast<cpx<T>*>(smem + 5 * TB + S::XBYTES);
+  unsigned char* u_buf = smem;
+  unsigned char* k_buf = smem + TB;
+  unsigned char* q_buf = smem + 2 * TB;
+  cpx<T>* xbuf = reinterpret_cast<cpx<T>*>(smem + 3 * TB);
+  cpx<T>* tws = reinterpret_cast<cpx<T>*>(smem + 3 * TB + S::XBYTES);
   const cpx<T>* twA = tws;
   const cpx<T>* twB = tws + L;
   stage_twiddles<T, L>(tws, a.twA, a.twB);
-  __shared__ uint64_t full[2], qbar;
+  __shared__ uint64_t ubar, kbar, qbar;
   const int g = threadIdx.x / TH, t = threadIdx.x % TH;
   cpx<T>* sm = xbuf + g * S::XSTRIDE;
   const long long ntiles = (long long)(a.g.n[2] / S::W) * (AXIS == 1 ? a.g.n[0] : a.g.n[1]);
   const T coef = T(a.c0 * (a.use_kf ? a.prm->k_f : 1.0) * a.prm->s / (double(L) * double(L)));
 
-  auto issue_uk = [&](long long tile, int b) {
+  auto issue = [&](unsigned char* dst, const CUtensorMap* map, uint64_t* bar, long long tile) {
     int c0, c1, c2;
     tile_coords(a.g, AXIS, S::W, tile, c0, c1, c2);
-    mbar_expect_tx(&full[b], 2 * TB);
-    tma_load3(u_st(b), &a.map_u, c0, c1, c2, &full[b]);
-    tma_load3(k_st(b), &a.map_k, c0, c1, c2, &full[b]);
-  };
-  auto issue_q = [&](long long tile) {
-    int c0, c1, c2;
-    tile_coords(a.g, AXIS, S::W, tile, c0, c1, c2);
-    mbar_expect_tx(&qbar, TB);
-    tma_load3(q_buf, &a.map_q, c0, c1, c2, &qbar);
+    mbar_expect_tx(bar, TB);
+    tma_load3(dst, map, c0, c1, c2, bar);
   };
 
   if (threadIdx.x == 0) {
-    mbar_init(&full[0], 1);
-    mbar_init(&full[1], 1);
+    mbar_init(&ubar, 1);
+    mbar_init(&kbar, 1);
     mbar_init(&qbar, 1);
     fence_barrier_init();
   }
   __syncthreads();
   const long long t0 = blockIdx.x, stride = gridDim.x;
-  if (threadIdx.x == 0) {
-    if (t0 < ntiles) {
-      issue_uk(t0, 0);
-      issue_q(t0);
-    }
-    if (t0 + stride < ntiles) issue_uk(t0 + stride, 1);
+  if (threadIdx.x == 0 && t0 < ntiles) {
+    issue(u_buf, &a.map_u, &ubar, t0);
+    issue(k_buf, &a.map_k, &kbar, t0);
+    issue(q_buf, &a.map_q, &qbar, t0);
   }
   double red = 0.0;
   bool bad = false;
   int i = 0;
   for (long long tile = t0; tile < ntiles; tile += stride, ++i) {
-    const int b = i & 1;
-    bool ok = mbar_wait(&full[b], (i >> 1) & 1);
+    const bool more = tile + stride < ntiles;
+    bool ok = mbar_wait(&ubar, i & 1);
     if (__syncthreads_or(!ok)) { bad = true; break; }
     cpx<T> v[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = *tile_pair<T>(u_st(b), idx_a<L>(r, t), g);
+    for (int r = 0; r < R; ++r) v[r] = *tile_pair<T>(u_buf, idx_a<L>(r, t), g);
+    __syncthreads();   // every u value is in registers
+    if (threadIdx.x == 0 && more) issue(u_buf, &a.map_u, &ubar, tile + stride);
     fft_ab<T, L, -1, true>(v, sm, t, twA);
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = times_ik(v[r], kwave<L>(idx_b<L>(r, t)));
     fft_ba<T, L, +1, true>(v, sm, t, twB);
+    ok = mbar_wait(&kbar, i & 1);
+    if (__syncthreads_or(!ok)) { bad = true; break; }
+    T loc = T(0);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-      cpx<T> k = *tile_pair<T>(k_st(b), idx_a<L>(r, t), g);
+      cpx<T> k = *tile_pair<T>(k_buf, idx_a<L>(r, t), g);
+      if (a.reduce) loc += k.x * v[r].x * v[r].x + k.y * v[r].y * v[r].y;
       v[r].x *= k.x;
       v[r].y *= k.y;
     }
+    red += double(loc);
+    __syncthreads();   // every kappa value is in registers
+    if (threadIdx.x == 0 && more) issue(k_buf, &a.map_k, &kbar, tile + stride);
     fft_ab<T, L, -1, true>(v, sm, t, twA);
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = times_ik(v[r], kwave<L>(idx_b<L>(r, t)));
     fft_ba<T, L, +1, true>(v, sm, t, twB);
     ok = mbar_wait(&qbar, i & 1);
     if (__syncthreads_or(!ok)) { bad = true; break; }
-    T loc = T(0);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       cpx<T>* qp = tile_pair<T>(q_buf, idx_a<L>(r, t), g);
       cpx<T> q = *qp;
       q.x += coef * v[r].x;
       q.y += coef * v[r].y;
-      if (a.reduce) {
-        cpx<T> u = *tile_pair<T>(u_st(b), idx_a<L>(r, t), g);
-        loc += u.x * q.x + u.y * q.y;
-      }
       *qp = q;
     }
-    red += double(loc);
     fence_proxy_async();
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -238,9 +239,8 @@ __global__ void __launch_bounds__(TmaShape<T, L>::THREADS) k_op_tma(const __grid
       tile_coords(a.g, AXIS, S::W, tile, c0, c1, c2);
       tma_store3(&a.map_q, q_buf, c0, c1, c2);
       bulk_commit();
-      if (tile + 2 * stride < ntiles) issue_uk(tile + 2 * stride, b);
       bulk_wait_read0();
-      if (tile + stride < ntiles) issue_q(tile + stride);
+      if (more) issue(q_buf, &a.map_q, &qbar, tile + stride);
     }
   }
   if (threadIdx.x == 0) bulk_wait0();
@@ -392,7 +392,7 @@ struct TmaRowShape {
   static constexpr int XBYTES = PAIRS * XSTRIDE * int(sizeof(cpx<T>));
   static constexpr bool OK = (THREADS >= 32) && (THREADS % 32 == 0);
   static constexpr int TWBYTES = 2 * L * int(sizeof(cpx<T>));
-  static constexpr size_t OPX_SMEM = 6 * size_t(TILE_BYTES) + XBYTES + TWBYTES + 1024;
+  static constexpr size_t OPX_SMEM = 4 * size_t(TILE_BYTES) + XBYTES + TWBYTES + 1024;
   static constexpr size_t UPD_SMEM = 8 * size_t(TILE_BYTES) + XBYTES + TWBYTES + 1024;
   static constexpr size_t SETUP_SMEM = 2 * size_t(TILE_BYTES) + XBYTES + TWBYTES + 1024;
 };
@@ -428,25 +428,30 @@ struct PcgOpxTmaArgs {
   const cpx<T>* twB;
   Params* prm;
   PcgState* st;
+  Fin fin;   // reduces |p|^2 and sum kappa (L d_2 p)^2 (kFinPqAdd)
 };
 
 // z = H_2(w); p = z + beta p; q = p - s k_f d_2(kappa d_2 p)  (fields written
-// at layout-B positions of each pencil).
+// at layout-B positions of each pencil); reduces |p|^2 and sum kappa
+// (L d_2 p)^2.  Buffers: w (single, the next tile's w is requested as soon as
+// this one is in registers), kappa (single; q is written into it once kappa
+// is in registers, the next kappa is requested after q's store), p (two
+// stages).
 template <typename T, int L>
 __global__ void __launch_bounds__(TmaRowShape<T, L>::THREADS) k_pcg_opx_tma(const __grid_constant__ PcgOpxTmaArgs<T> a) {
   using S = TmaRowShape<T, L>;
   constexpr int R = S::R, TH = S::TH, TB = S::TILE_BYTES;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  auto w_st = [&](int b) { return smem + b * TB; };
-  auto k_st = [&](int b) { return smem + (2 + b) * TB; };
-  auto p_st = [&](int b) { return smem + (4 + b) * TB; };
-  cpx<T>* xbuf = reinterpret_cast<cpx<T>*>(smem + 6 * TB);
-  cpx<T>* tws = reinterpret_cast<cpx<T>*>(smem + 6 * TB + S::XBYTES);
+  unsigned char* w_buf = smem;
+  unsigned char* k_buf = smem + TB;   // kappa, then q
+  auto p_st = [&](int b) { return smem + (2 + b) * TB; };
+  cpx<T>* xbuf = reinterpret_cast<cpx<T>*>(smem + 4 * TB);
+  cpx<T>* tws = reinterpret_cast<cpx<T>*>(smem + 4 * TB + S::XBYTES);
   const cpx<T>* twA = tws;
   const cpx<T>* twB = tws + L;
   stage_twiddles<T, L>(tws, a.twA, a.twB);
-  __shared__ uint64_t full[2];
+  __shared__ uint64_t wbar, kbar, pbar[2];
   const int g = threadIdx.x / TH, t = threadIdx.x % TH;
   cpx<T>* sm = xbuf + g * S::XSTRIDE;
   const long long ntiles = a.g.nn / L / S::ROWS;
@@ -454,39 +459,51 @@ __global__ void __launch_bounds__(TmaRowShape<T, L>::THREADS) k_pcg_opx_tma(cons
   const bool use_p = (betad != 0.0);
   const T beta = T(betad);
   const T coef = T(-a.prm->s * a.prm->k_f / (double(L) * double(L)));
-  auto issue = [&](long long tile, int b) {
-    const int row0 = int(tile * S::ROWS);
-    mbar_expect_tx(&full[b], (use_p ? 3 : 2) * TB);
-    tma_load2(w_st(b), &a.map_w, 0, row0, &full[b]);
-    tma_load2(k_st(b), &a.map_k, 0, row0, &full[b]);
-    if (use_p) tma_load2(p_st(b), &a.map_p, 0, row0, &full[b]);
+  auto issue = [&](unsigned char* dst, const CUtensorMap* map, uint64_t* bar, long long tile) {
+    mbar_expect_tx(bar, TB);
+    tma_load2(dst, map, 0, int(tile * S::ROWS), bar);
   };
   if (threadIdx.x == 0) {
-    mbar_init(&full[0], 1);
-    mbar_init(&full[1], 1);
+    mbar_init(&wbar, 1);
+    mbar_init(&kbar, 1);
+    mbar_init(&pbar[0], 1);
+    mbar_init(&pbar[1], 1);
     fence_barrier_init();
   }
   __syncthreads();
   const long long t0 = blockIdx.x, stride = gridDim.x;
-  if (threadIdx.x == 0) {
-    if (t0 < ntiles) issue(t0, 0);
-    if (t0 + stride < ntiles) issue(t0 + stride, 1);
+  if (threadIdx.x == 0 && t0 < ntiles) {
+    issue(w_buf, &a.map_w, &wbar, t0);
+    issue(k_buf, &a.map_k, &kbar, t0);
+    if (use_p) {
+      issue(p_st(0), &a.map_p, &pbar[0], t0);
+      if (t0 + stride < ntiles) issue(p_st(1), &a.map_p, &pbar[1], t0 + stride);
+    }
   }
   bool bad = false;
+  double red_pp = 0.0, red_k = 0.0;
   int i = 0;
   const int ra = 2 * g, rb = 2 * g + 1;
   for (long long tile = t0; tile < ntiles; tile += stride, ++i) {
     const int b = i & 1;
-    bool ok = mbar_wait(&full[b], (i >> 1) & 1);
+    const bool more = tile + stride < ntiles;
+    bool ok = mbar_wait(&wbar, i & 1);
     if (__syncthreads_or(!ok)) { bad = true; break; }
     cpx<T> v[R];
+    T lpp = T(0), lk = T(0);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const int n = idx_a<L>(r, t);
-      v[r] = {*row_elem<T, L>(w_st(b), ra, n), *row_elem<T, L>(w_st(b), rb, n)};
+      v[r] = {*row_elem<T, L>(w_buf, ra, n), *row_elem<T, L>(w_buf, rb, n)};
     }
+    __syncthreads();   // every w value is in registers
+    if (threadIdx.x == 0 && more) issue(w_buf, &a.map_w, &wbar, tile + stride);
     fft_ab<T, L, -1, true>(v, sm, t, twA);
     hartley_combine<T, L, true>(v, t);
+    if (use_p) {
+      ok = mbar_wait(&pbar[b], (i >> 1) & 1);
+      if (__syncthreads_or(!ok)) { bad = true; break; }
+    }
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const int n = idx_b<L>(r, t);
@@ -496,6 +513,7 @@ __global__ void __launch_bounds__(TmaRowShape<T, L>::THREADS) k_pcg_opx_tma(cons
         v[r].x += beta * *pa;
         v[r].y += beta * *pb;
       }
+      lpp += v[r].x * v[r].x + v[r].y * v[r].y;
       *pa = v[r].x;
       *pb = v[r].y;
     }
@@ -503,12 +521,19 @@ __global__ void __launch_bounds__(TmaRowShape<T, L>::THREADS) k_pcg_opx_tma(cons
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = times_ik(v[r], kwave<L>(idx_a<L>(r, t)));
     fft_ab<T, L, +1, true>(v, sm, t, twA);
+    ok = mbar_wait(&kbar, i & 1);
+    if (__syncthreads_or(!ok)) { bad = true; break; }
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const int n = idx_b<L>(r, t);
-      v[r].x *= *row_elem<T, L>(k_st(b), ra, n);
-      v[r].y *= *row_elem<T, L>(k_st(b), rb, n);
+      const T ka = *row_elem<T, L>(k_buf, ra, n), kb = *row_elem<T, L>(k_buf, rb, n);
+      lk += ka * v[r].x * v[r].x + kb * v[r].y * v[r].y;
+      v[r].x *= ka;
+      v[r].y *= kb;
     }
+    red_pp += double(lpp);
+    red_k += double(lk);
+    __syncthreads();   // kappa consumed: its tile now receives q
     fft_ba<T, L, -1, true>(v, sm, t, twB);
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = times_ik(v[r], kwave<L>(idx_a<L>(r, t)));
@@ -516,22 +541,28 @@ __global__ void __launch_bounds__(TmaRowShape<T, L>::THREADS) k_pcg_opx_tma(cons
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const int n = idx_b<L>(r, t);
-      *row_elem<T, L>(w_st(b), ra, n) = *row_elem<T, L>(p_st(b), ra, n) + coef * v[r].x;
-      *row_elem<T, L>(w_st(b), rb, n) = *row_elem<T, L>(p_st(b), rb, n) + coef * v[r].y;
+      *row_elem<T, L>(k_buf, ra, n) = *row_elem<T, L>(p_st(b), ra, n) + coef * v[r].x;
+      *row_elem<T, L>(k_buf, rb, n) = *row_elem<T, L>(p_st(b), rb, n) + coef * v[r].y;
     }
     fence_proxy_async();
     __syncthreads();
     if (threadIdx.x == 0) {
       const int row0 = int(tile * S::ROWS);
       tma_store2(&a.map_p, p_st(b), 0, row0);
-      tma_store2(&a.map_q, w_st(b), 0, row0);
+      tma_store2(&a.map_q, k_buf, 0, row0);
       bulk_commit();
       bulk_wait_read0();
-      if (tile + 2 * stride < ntiles) issue(tile + 2 * stride, b);
+      if (more) issue(k_buf, &a.map_k, &kbar, tile + stride);
+      if (use_p && tile + 2 * stride < ntiles) issue(p_st(b), &a.map_p, &pbar[b], tile + 2 * stride);
     }
   }
   if (threadIdx.x == 0) bulk_wait0();
-  if (bad && threadIdx.x == 0) { a.st->status = kStTimeout; a.st->sticky = kStTimeout; }
+  if (bad) {
+    if (threadIdx.x == 0) { a.st->status = kStTimeout; a.st->sticky = kStTimeout; }
+    return;
+  }
+  double vv[2] = {red_pp, red_k};
+  reduce_finish<2>(vv, a.fin);
 }
 
 template <typename T>
