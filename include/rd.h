@@ -191,6 +191,16 @@ void rd_profile_enable(int on);
 int rd_profile_read(double* ms, long long* launches, int n);
 const char* rd_profile_class(int i);
 
+/* Autotuner: on this context's grid, time `reps` PCG iterations for each
+ * candidate persistent-grid size (all resident blocks, or 1..8 blocks per
+ * SM) and keep the fastest per kernel class; the choice applies to every
+ * later launch in the process.  caps (may be NULL) receives, per class of
+ * rd_profile_class, the chosen block count (0 = all resident blocks).
+ * Leaves the PCG work fields modified (not the state, data or trajectory). */
+rd_status rd_autotune(rd_ctx* ctx, int reps, int* caps, int ncaps);
+/* Forget every autotuner choice (back to all resident blocks). */
+void rd_autotune_clear(void);
+
 /* Message of the last failing call ("" if none). */
 const char* rd_last_error(const rd_ctx* ctx);
 

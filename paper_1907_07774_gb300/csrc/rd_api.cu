@@ -14,6 +14,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <atomic>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -144,6 +145,14 @@ bool row_map(CUtensorMap* out, const void* ptr, const Geom& g, int esz, int rows
 
 bool prof_active() { return prof().on; }
 
+namespace {
+std::atomic<int> g_tuned_cap[kcCount];
+}
+int tuned_cap(int cls) { return (cls >= 0 && cls < kcCount) ? g_tuned_cap[cls].load() : 0; }
+void set_tuned_cap(int cls, int cap) {
+  if (cls >= 0 && cls < kcCount) g_tuned_cap[cls].store(cap < 0 ? 0 : cap);
+}
+
 int prof_begin(int cls, cudaStream_t s) {
   Profiler& p = prof();
   if (!p.on) return -1;
@@ -229,6 +238,7 @@ struct EngineBase {
   virtual rd_status batch_enqueue(const double*, double, double, cudaStream_t) = 0;
   virtual rd_status batch_finish(double*, double*) = 0;
   virtual void batch_prepare(const double*, double, double) = 0;
+  virtual rd_status autotune(int, int*, int) = 0;
   virtual bool warm() const = 0;
 };
 
@@ -1051,6 +1061,59 @@ struct Engine : EngineBase {
     return s;
   }
 
+  // ---- autotuner --------------------------------------------------------
+  // Times `reps` PCG iterations on this context's buffers for each
+  // candidate persistent-grid size (multiples of the SM count) and keeps,
+  // per kernel class, the fastest.  The choices apply to every later launch
+  // in the process.
+  rd_status autotune(int reps, int* caps_out, int ncls) override {
+    if (!have_tissue) return fail(RD_ERR_STATE, "rd_set_tissue is required");
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int kClasses[] = {kcOpStrided, kcPcgOpx, kcDhtPlain, kcDhtSym, kcDhtUpdate};
+    std::vector<int> cands = {0};   // 0: all resident blocks
+    for (int m = 1; m <= 8; ++m) cands.push_back(m * sms);
+    double best[kcCount];
+    int best_cap[kcCount];
+    for (int c = 0; c < kcCount; ++c) {
+      best[c] = 1e300;
+      best_cap[c] = tuned_cap(c);
+    }
+    cudaError_t e;
+    hprm->k_f = (hprm->k_f > 0.0) ? hprm->k_f : 0.05;
+    if ((e = upload_params()) != cudaSuccess) return cuda_fail(e, "upload params");
+    // a smooth right-hand side: f = A kappa1
+    if ((e = apply3(f[F_KAPPA1], f[F_R], 1.0, 1)) != cudaSuccess) return cuda_fail(e, "tune rhs");
+    for (int cap : cands) {
+      for (int c : kClasses) set_tuned_cap(c, cap);
+      if ((e = apply3(f[F_KAPPA1], f[F_R], 1.0, 1)) != cudaSuccess) return cuda_fail(e, "tune rhs");
+      if ((e = enqueue_setup(0)) != cudaSuccess) return cuda_fail(e, "tune setup");
+      if ((e = enqueue_iteration(0)) != cudaSuccess) return cuda_fail(e, "tune warm");
+      rd_profile_enable(1);
+      for (int r = 0; r < reps; ++r)
+        if ((e = enqueue_iteration(0)) != cudaSuccess) {
+          rd_profile_enable(0);
+          return cuda_fail(e, "tune iteration");
+        }
+      double ms[kcCount];
+      long long cnt[kcCount];
+      rd_profile_read(ms, cnt, kcCount);
+      rd_profile_enable(0);
+      for (int c : kClasses)
+        if (cnt[c] > 0 && ms[c] / cnt[c] < best[c]) {
+          best[c] = ms[c] / cnt[c];
+          best_cap[c] = cap;
+        }
+    }
+    for (int c : kClasses) set_tuned_cap(c, best_cap[c]);
+    for (int c = 0; c < ncls && caps_out; ++c) caps_out[c] = tuned_cap(c);
+    // leave the PCG state clean for the next solve
+    if ((e = cudaMemsetAsync(&st->total_it, 0, 2 * sizeof(int), stream)) != cudaSuccess) return cuda_fail(e, "reset");
+    if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_fail(e, "sync");
+    return RD_OK;
+  }
+
   // ---- batched gradient -------------------------------------------------
   bool warm() const override { return host_solves >= 2; }
 
@@ -1482,6 +1545,15 @@ rd_status rd_batch_gradient(rd_ctx* const* ctxs, int count, const double* const*
 
 int rd_last_pcg_iters(const rd_ctx* c) { return c ? c->e->last_iters : 0; }
 int rd_last_graph_solves(const rd_ctx* c) { return c ? c->e->last_graph_solves : 0; }
+
+void rd_autotune_clear(void) {
+  for (int c = 0; c < rd::kcCount; ++c) rd::set_tuned_cap(c, 0);
+}
+
+rd_status rd_autotune(rd_ctx* c, int reps, int* caps, int ncaps) {
+  if (!c || reps < 1) return RD_ERR_ARG;
+  return c->e->autotune(reps, caps, ncaps);
+}
 int rd_last_pcg_solves(const rd_ctx* c) { return c ? c->e->last_solves : 0; }
 
 const char* rd_last_error(const rd_ctx* c) { return c ? c->e->err : "null context"; }

@@ -19,6 +19,10 @@ enum KClass {
 // stream; prof_begin returns a token for prof_end (-1 when off).
 int prof_begin(int cls, cudaStream_t s);
 bool prof_active();
+// Grid-size choices made by the autotuner, per kernel class (0: none, the
+// launcher then uses every block that fits on the device).
+int tuned_cap(int cls);
+void set_tuned_cap(int cls, int cap);
 // Tensor map for TMA tiles of a strided pass: box {64 B of i2, L along the
 // axis}, 64-byte swizzle.  Cached per (pointer, grid, element size, axis);
 // false if the map cannot be made (the caller then uses the direct kernels).

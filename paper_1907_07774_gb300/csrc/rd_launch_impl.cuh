@@ -54,6 +54,8 @@ cudaError_t launch_pencil(K kern, size_t smem, long long groups_needed, const A&
                           int cls = kcOther) {
   const void* fn = reinterpret_cast<const void*>(kern);
   int grid = grid_for(fn, smem, groups_needed);
+  const int tc = tuned_cap(cls);
+  if (tc > 0 && tc < grid) grid = tc;
   const int tok = prof_begin(cls, s);
   kern<<<grid, kThreads, smem, s>>>(a);
   cudaError_t e = cudaGetLastError();
@@ -103,6 +105,8 @@ cudaError_t launch_tma(K kern, size_t smem, int threads, long long tiles, const 
       cap = it->second;
     }
   }
+  const int tc = tuned_cap(cls);
+  if (tc > 0 && tc < cap) cap = tc;
   const int grid = (int)(tiles < cap ? tiles : cap);
   const int tok = prof_begin(cls, s);
   kern<<<grid, threads, smem, s>>>(a);

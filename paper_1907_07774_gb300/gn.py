@@ -65,22 +65,39 @@ def project(theta):
 
 
 def gauss_newton(solver, theta0, iters=10, cg_maxit=20, armijo_c=1e-4, max_backtracks=12, gtol=1e-6,
-                 callback=None):
+                 forcing=None, scale=None, callback=None):
     """Run ``iters`` Gauss-Newton iterations from ``theta0 = [p, k_f, rho_f]``
-    with a context that has tissue, basis and data set."""
+    with a context that has tissue, basis and data set.
+
+    CG runs on the system rescaled by ``scale`` (default: 1 for p and the
+    initial magnitudes of k_f and rho_f, whose natural units differ by orders
+    of magnitude), i.e. on S H S with S = diag(scale).  ``forcing``: CG
+    relative tolerance; None gives Eisenstat-Walker
+    ``min(0.5, sqrt(|g| / |g_0|))``, a number fixes it (with ``cg_maxit``
+    the Newton step then uses up to that many Hessian-vector products)."""
     npar = solver.np
     theta = np.asarray(theta0, dtype=np.float64).copy()
     split = lambda th: (th[:npar], th[npar], th[npar + 1])
+    if scale is None:
+        scale = np.ones_like(theta)
+        scale[npar] = max(abs(theta[npar]), 1e-3)
+        scale[npar + 1] = max(abs(theta[npar + 1]), 1e-3)
+    scale = np.asarray(scale, dtype=np.float64)
     J, g = solver.rd_gradient(*split(theta))
-    g0 = float(np.linalg.norm(g))
+    g0 = float(np.linalg.norm(scale * g))
     hist = []
     for k in range(iters):
         t0 = time.perf_counter()
         gn = float(np.linalg.norm(g))
-        if gn <= gtol or gn <= 1e-12 * max(g0, 1e-300):
+        gs = scale * g
+        if gn <= gtol or float(np.linalg.norm(gs)) <= 1e-12 * max(g0, 1e-300):
             break
-        eta = min(0.5, np.sqrt(gn / g0)) if g0 > 0 else 0.5
-        d, n_hv = cg(lambda v: solver.rd_hessvec(*split(theta), v), -g, cg_maxit, eta)
+        if forcing is None:
+            eta = min(0.5, np.sqrt(float(np.linalg.norm(gs)) / g0)) if g0 > 0 else 0.5
+        else:
+            eta = float(forcing)
+        ds, n_hv = cg(lambda v: scale * solver.rd_hessvec(*split(theta), scale * v), -gs, cg_maxit, eta)
+        d = scale * ds
         slope = float(g @ d)
         if slope >= 0.0:
             d, slope = -g, -gn * gn

@@ -62,6 +62,8 @@ def lib():
         "rd_last_pcg_solves": ([vp], ci),
         "rd_last_graph_solves": ([vp], ci),
         "rd_batch_gradient": ([vp, ci, vp, vp, vp, vp, vp], st),
+        "rd_autotune": ([vp, ci, vp, ci], st),
+        "rd_autotune_clear": ([], None),
         "rd_last_error": ([vp], ctypes.c_char_p),
         "rd_destroy": ([vp], None),
         "rd_apply_precond_static": ([vp, cd, vp, vp, vp], st),
@@ -79,6 +81,10 @@ def lib():
 
 def rd_profile_enable(on):
     lib().rd_profile_enable(1 if on else 0)
+
+
+def rd_autotune_clear():
+    lib().rd_autotune_clear()
 
 
 def rd_profile_read():
@@ -259,6 +265,14 @@ class Context:
 
     def rd_last_pcg_iters(self):
         return lib().rd_last_pcg_iters(self.h)
+
+    def rd_autotune(self, reps=3):
+        """Tune grid sizes per kernel class on this grid; returns
+        {class: blocks (0 = all resident)}."""
+        n = 16
+        caps = (ctypes.c_int * n)()
+        self._call(lib().rd_autotune(self.h, int(reps), caps, n))
+        return {lib().rd_profile_class(i).decode(): caps[i] for i in range(10)}
 
     def rd_last_graph_solves(self):
         return lib().rd_last_graph_solves(self.h)

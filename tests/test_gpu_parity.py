@@ -330,3 +330,17 @@ def test_batch_gradient_of_uneven_problems_matches_single_gradients():
         for (Jw, gw), J, g, c in zip(want, Js, gs, ctxs):
             assert J == Jw and np.array_equal(g, gw)
             assert c.rd_last_graph_solves() == c.rd_last_pcg_solves() > 0
+
+
+def test_autotuned_grid_sizes_keep_parity():
+    prob, M, d = _grad_case(n=(32, 32, 32))
+    J_or, g_or, _, _ = M.gradient(prob.p, prob.k_f, prob.rho_f, d)
+    ctx = gpu_for(prob, "mixed")
+    ctx.rd_set_data(d)
+    try:
+        caps = ctx.rd_autotune(reps=2)
+        assert set(caps) >= {"op_axis01", "pcg_opx", "dht_plain", "dht_sym", "dht_update"}
+        J, g = ctx.rd_gradient(prob.p, prob.k_f, prob.rho_f)
+        assert rel(g, g_or) <= TOL["mixed"] and abs(J - J_or) <= TOL["mixed"] * J_or
+    finally:
+        R.rd_autotune_clear()
