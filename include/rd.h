@@ -77,6 +77,10 @@ typedef struct {
   double k_w[3];     /* k_i of Eq. coeff_tumor (WM, GM, CSF)                */
   double rho_w[3];   /* rho_i of Eq. coeff_tumor                            */
   double beta_p;     /* weight of 1/2 |p|^2 in the objective                 */
+  int moving_atlas;  /* 1: reserve fields for the Moving-Atlas anatomy misfit
+                        (rd_set_anatomy_data); 0: tumor misfit only          */
+  int coupling;      /* 1: keep the per-voxel adjoint integrands for
+                        rd_coupling_field (two more fields); 0: off          */
 } rd_config;
 
 /* Fill *cfg with defaults: 64^3, nt 16, t_end 1, FP64, rtol 1e-10, maxit
@@ -104,6 +108,28 @@ rd_status rd_set_basis(rd_ctx* ctx, const double* centers, double sigma);
 
 /* Target data d (FP64 field) for the misfit. */
 rd_status rd_set_data(rd_ctx* ctx, const double* d);
+
+/* Moving-Atlas objective (Eq. objective_tu): patient anatomy labels
+ * m_D = (m_D,WM, m_D,GM, m_D,CSF), FP64 fields, host or device.  Needs
+ * cfg.moving_atlas = 1.  From then on the misfit is
+ * D_c + D_m = 1/2 h^3 sum (c(1) - d)^2 + 1/2 h^3 sum_i sum (m_i (1 - c(1)) - m_D,i)^2
+ * with m the tissue maps of rd_set_tissue, the adjoint final condition is
+ * alpha(1) = d - c(1) + m^T (m (1 - c(1)) - m_D) (Eq. tumor:adj-final), and
+ * rd_hessvec weights the tangent c(1) by 1 + sum_i m_i^2. */
+rd_status rd_set_anatomy_data(rd_ctx* ctx, const double* md_wm, const double* md_gm, const double* md_csf);
+
+/* Picard coupling field of the registration step (Sec. 2.2):
+ *   q_i(x) = int_0^1 kbar_i grad c . grad alpha + rhobar_i c (1 - c) alpha dt,
+ * kbar = k_f k_w, rhobar = rho_f rho_w, for the (p, k_f, rho_f) of the last
+ * rd_gradient / rd_adjoint / rd_batch_gradient, with the time quadrature
+ * of the discrete gradient and the sign of a derivative: a change dm of the
+ * tissue maps inside the coefficients (Eq. coeff_tumor) changes the
+ * objective by h^3 sum_x sum_i q_i dm_i at first order.  Writes three FP64
+ * fields (host or device, n0*n1*n2 each, z fastest).  Needs cfg.coupling = 1;
+ * RD_ERR_STATE before a gradient or after anything that invalidates it
+ * (a later rd_forward, or rd_hessvec at other parameters, new tissue, data
+ * or anatomy data). */
+rd_status rd_coupling_field(rd_ctx* ctx, double* q_wm, double* q_gm, double* q_csf);
 
 /* State solve (Eq. tumor:fwd): c(1) for parameters (p, k_f, rho_f); p is a
  * host array of np values.  c1_out (FP64 field, may be NULL) receives c(1);

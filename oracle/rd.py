@@ -21,7 +21,11 @@ It computes, plainly and slowly, in FP64:
   ``tumor:inv_diff``) and ``rho_f`` (derived the same way from Eq.
   ``coeff_tumor``);
 * the Gauss-Newton Hessian-vector product ``J^T J v`` built from the tangent
-  linear model and the same adjoint.
+  linear model and the same adjoint;
+* the Moving-Atlas anatomy misfit ``D_m`` and its final-condition term
+  (Eq. ``objective_tu``, ``tumor:adj-final``);
+* the Picard coupling field ``q(x)`` handed to the registration step
+  (Sec. 2.2).
 
 Readings where the paper is silent (each also listed in the design doc):
 
@@ -37,6 +41,11 @@ Readings where the paper is silent (each also listed in the design doc):
 * Gaussians ``exp(-|x - x_i|^2 / (2 sigma^2))`` with the minimum-image
   distance per axis and peak value 1; no CSF zeroing unless requested.
 * Misfit weight ``h^3`` (the L2(Omega) quadrature of ``D_c``).
+
+Moving-Atlas objective (Eq. ``objective_tu``, optional): with anatomy data
+``m_D`` set, the misfit adds ``D_m = 1/2 ||m (1 - c(1)) - m_D||^2`` summed
+over the three labels, and the adjoint final condition adds
+``m^T (m (1 - c(1)) - m_D)`` (Eq. ``tumor:adj-final``).
 """
 
 from __future__ import annotations
@@ -192,6 +201,10 @@ class Model:
         self.rho1 = rho_w[0] * m[0] + rho_w[1] * m[1] + rho_w[2] * m[2]
         self.g = gaussian_factors(self.n, centers, sigma)
         self.csf = (m[2] < 0.5).astype(np.float64) if csf_zero else None
+        self.m = m
+        self.k_w = tuple(float(x) for x in k_w)
+        self.rho_w = tuple(float(x) for x in rho_w)
+        self.m_data = None
         self.nt = int(nt)
         self.tau = t_end / nt
         self.s = 0.5 * self.tau
@@ -239,35 +252,72 @@ class Model:
             c = c_next
         return c, traj
 
+    def set_anatomy_data(self, m_d):
+        """Patient anatomy labels ``m_D`` (three fields) for ``D_m``."""
+        self.m_data = [np.asarray(x, dtype=np.float64) for x in m_d]
+
     def misfit(self, c1, d, p):
         r = c1 - d
-        return 0.5 * self.h3 * float(np.sum(r * r)) \
-            + 0.5 * self.beta_p * float(np.dot(p, p))
+        J = 0.5 * self.h3 * float(np.sum(r * r)) + 0.5 * self.beta_p * float(np.dot(p, p))
+        if self.m_data is not None:
+            for mi, mdi in zip(self.m, self.m_data):
+                e = mi * (1.0 - c1) - mdi
+                J += 0.5 * self.h3 * float(np.sum(e * e))
+        return J
+
+    def final_adjoint(self, c1, d):
+        """``alpha(1) = d - c(1) [+ m^T (m (1 - c(1)) - m_D)]``."""
+        a = d - c1
+        if self.m_data is not None:
+            for mi, mdi in zip(self.m, self.m_data):
+                a = a + mi * (mi * (1.0 - c1) - mdi)
+        return a
+
+    def final_weight(self):
+        """Second derivative of the misfit in c(1): 1 [+ sum_i m_i^2]."""
+        w = 1.0
+        if self.m_data is not None:
+            w = w + sum(mi * mi for mi in self.m)
+        return w
 
     # -- adjoint (Eq. tumor:adj, tumor:adj-final) and gradient assembly -----
-    def adjoint(self, traj, alpha1, k_f, rho_f):
+    def adjoint(self, traj, alpha1, k_f, rho_f, fields=None):
         """Reverse sweep of the discrete adjoint from ``alpha(1)``.
 
         Returns ``(alpha(0), g_kf, g_rhof)`` where, with ``s = tau/2`` and
         ``abar`` the CN-transposed adjoint of each step,
         ``g_kf = sum_n s h^3 sum_x kappa1 grad(abar) . grad(c* + c**)``
         (trapezoidal form of Eq. ``tumor:inv_diff``) and
-        ``g_rhof = -sum_half-steps h^3 sum_x alpha s rho1 L (1 - L)``."""
+        ``g_rhof = -sum_half-steps h^3 sum_x alpha s rho1 L (1 - L)``.
+
+        ``fields``: a dict that receives the same integrands before the sum
+        over x, ``"k"`` = ``sum_n s grad(abar) . grad(c* + c**)`` and
+        ``"rho"`` = ``-sum_half-steps s alpha L (1 - L)`` per voxel, so that
+        ``g_kf = h^3 sum_x kappa1 fields["k"]`` and likewise for rho_f."""
         rho = rho_f * self.rho1
         s, h3 = self.s, self.h3
         alpha = np.array(alpha1, dtype=np.float64)
         g_kf = 0.0
         g_rho = 0.0
+        qk = np.zeros(self.n)
+        qr = np.zeros(self.n)
         for c, c_star, c_ss, c_next in reversed(traj):
+            qr -= alpha * s * c_next * (1.0 - c_next)
             g_rho -= h3 * float(np.sum(alpha * s * self.rho1 * c_next * (1.0 - c_next)))
             alpha_ss = logistic_dc(c_ss, rho, s) * alpha
             abar = self.solve(alpha_ss, alpha_ss, k_f)
             ga = self.sp.grad(abar)
             gw = self.sp.grad(c_star + c_ss)
-            g_kf += s * h3 * float(np.sum(self.kappa1 * (ga[0] * gw[0] + ga[1] * gw[1] + ga[2] * gw[2])))
+            dot = ga[0] * gw[0] + ga[1] * gw[1] + ga[2] * gw[2]
+            qk += s * dot
+            g_kf += s * h3 * float(np.sum(self.kappa1 * dot))
             alpha_star = abar + s * self.A(abar, k_f)
+            qr -= alpha_star * s * c_star * (1.0 - c_star)
             g_rho -= h3 * float(np.sum(alpha_star * s * self.rho1 * c_star * (1.0 - c_star)))
             alpha = logistic_dc(c, rho, s) * alpha_star
+        if fields is not None:
+            fields["k"] = qk
+            fields["rho"] = qr
         return alpha, g_kf, g_rho
 
     def gradient(self, p, k_f, rho_f, d):
@@ -276,9 +326,23 @@ class Model:
         p = np.asarray(p, dtype=np.float64)
         c1, traj = self.forward(p, k_f, rho_f)
         J = self.misfit(c1, d, p)
-        alpha0, g_kf, g_rho = self.adjoint(traj, d - c1, k_f, rho_f)
+        alpha0, g_kf, g_rho = self.adjoint(traj, self.final_adjoint(c1, d), k_f, rho_f)
         g_p = -self.h3 * self.phi_t(alpha0) + self.beta_p * p
         return J, np.concatenate([g_p, [g_kf, g_rho]]), c1, alpha0
+
+    def coupling(self, p, k_f, rho_f, d):
+        """Picard coupling field ``q = (q_WM, q_GM, q_CSF)`` of Sec. 2.2: the
+        time integral of ``kbar grad c . grad alpha + rhobar c (1 - c) alpha``
+        with ``kbar = k_f (k_WM, k_GM, k_CSF)`` and ``rhobar = rho_f (rho_WM,
+        rho_GM, rho_CSF)``, taken with the quadrature of the discrete
+        gradient and the sign of a derivative, so that a change of the tissue
+        maps inside the coefficients (Eq. ``coeff_tumor``) changes the
+        objective by ``h^3 sum_x q . dm`` at first order."""
+        p = np.asarray(p, dtype=np.float64)
+        c1, traj = self.forward(p, k_f, rho_f)
+        fl = {}
+        self.adjoint(traj, self.final_adjoint(c1, d), k_f, rho_f, fields=fl)
+        return [k_f * self.k_w[i] * fl["k"] + rho_f * self.rho_w[i] * fl["rho"] for i in range(3)]
 
     # -- Gauss-Newton Hessian-vector product --------------------------------
     def tangent(self, traj, v, k_f, rho_f):
@@ -300,13 +364,14 @@ class Model:
         return ch
 
     def hessvec(self, p, k_f, rho_f, v, traj=None):
-        """``H_GN v = J^T (h^3 J v) + beta_p v_p``."""
+        """``H_GN v = J^T (h^3 W J v) + beta_p v_p`` with W the second
+        derivative of the misfit in c(1) (1, plus sum m_i^2 with D_m)."""
         p = np.asarray(p, dtype=np.float64)
         v = np.asarray(v, dtype=np.float64)
         if traj is None:
             _, traj = self.forward(p, k_f, rho_f)
         ch1 = self.tangent(traj, v, k_f, rho_f)
-        alpha0, g_kf, g_rho = self.adjoint(traj, -ch1, k_f, rho_f)
+        alpha0, g_kf, g_rho = self.adjoint(traj, -self.final_weight() * ch1, k_f, rho_f)
         npar = len(v) - 2
         hv_p = -self.h3 * self.phi_t(alpha0) + self.beta_p * v[:npar]
         return np.concatenate([hv_p, [g_kf, g_rho]])

@@ -208,6 +208,8 @@ enum Field {
   F_KAPPA1, F_RHO1, F_C0, F_D, F_ALPHA, F_AB, F_WS, F_CN, F_CS,
   F_X, F_R, F_P, F_Q, F_W1, F_W2, F_CH, F_CHS, F_U, F_COUNT
 };
+constexpr int kAnatomyFields = 6;   // m_WM, m_GM, m_CSF, m_D,WM, m_D,GM, m_D,CSF
+constexpr int kCouplingFields = 2;  // per-voxel k_f and rho_f integrands of the adjoint
 
 }  // namespace
 
@@ -221,7 +223,7 @@ struct EngineBase {
   char err[512] = {0};
   int last_iters = 0, last_solves = 0, last_graph_solves = 0;
   bool capturing = false;   // enqueue into a stream capture (batch graph)
-  bool have_tissue = false, have_basis = false, have_data = false;
+  bool have_tissue = false, have_basis = false, have_data = false, have_mdata = false;
   bool have_traj = false, have_grad = false;
   double theta_kf = 0, theta_rho = 0;
   std::vector<double> theta_p, last_grad;
@@ -230,6 +232,8 @@ struct EngineBase {
   virtual rd_status set_tissue(const double*, const double*, const double*) = 0;
   virtual rd_status set_basis(const double*, double) = 0;
   virtual rd_status set_data(const double*) = 0;
+  virtual rd_status set_anatomy_data(const double*, const double*, const double*) = 0;
+  virtual rd_status coupling_field(double*, double*, double*) = 0;
   virtual rd_status forward(const double*, double, double, double*, double*) = 0;
   virtual rd_status adjoint(double*) = 0;
   virtual rd_status hessvec(const double*, double, double, const double*, double*) = 0;
@@ -261,6 +265,10 @@ struct Engine : EngineBase {
   double* phit_part = nullptr;
   double* stage[3] = {};
   T* f[F_COUNT] = {};
+  T* anat[kAnatomyFields] = {};   // Moving-Atlas fields (cfg.moving_atlas)
+  T* qf[kCouplingFields] = {};    // coupling integrands (cfg.coupling)
+  bool have_q = false;
+  double q_kf = 0.0, q_rho = 0.0;
   std::vector<T*> slots;   // checkpoint storage
   int nmax = 0;
   double sigma = 0;
@@ -302,6 +310,10 @@ struct Engine : EngineBase {
     put(e ? (void**)&e->phit_part : &dummy, sizeof(double) * size_t(np) * cfg.n[0]);
     for (int i = 0; i < 3; ++i) put(e ? (void**)&e->stage[i] : &dummy, sizeof(double) * nn);
     for (int i = 0; i < F_COUNT; ++i) put(e ? (void**)&e->f[i] : &dummy, sizeof(T) * nn);
+    if (cfg.moving_atlas)
+      for (int i = 0; i < kAnatomyFields; ++i) put(e ? (void**)&e->anat[i] : &dummy, sizeof(T) * nn);
+    if (cfg.coupling)
+      for (int i = 0; i < kCouplingFields; ++i) put(e ? (void**)&e->qf[i] : &dummy, sizeof(T) * nn);
     int nslots;
     if (cfg.ckpt_stride <= 0 || cfg.ckpt_stride >= cfg.nt) {
       nslots = cfg.nt;
@@ -706,6 +718,11 @@ struct Engine : EngineBase {
     a.rho1 = f[F_RHO1];
     a.nn = nn;
     a.prm = prm;
+    if (have_mdata)
+      for (int j = 0; j < 3; ++j) {
+        a.m[j] = anat[j];
+        a.md[j] = anat[3 + j];
+      }
     return a;
   }
 
@@ -770,6 +787,7 @@ struct Engine : EngineBase {
   }
 
   rd_status run_forward(const double* p, double k_f, double rho_f) {
+    have_q = false;
     cudaError_t e;
     rd_status rs;
     if (!have_tissue || !have_basis) return fail(RD_ERR_STATE, "rd_set_tissue and rd_set_basis are required");
@@ -840,7 +858,7 @@ struct Engine : EngineBase {
     return RD_OK;
   }
 
-  rd_status adj_step(int n) {
+  rd_status adj_step(int n, bool acc_q) {
     cudaError_t e;
     rd_status rs;
     const T* prev;
@@ -855,6 +873,7 @@ struct Engine : EngineBase {
     a.out0 = f[F_AB];
     a.out1 = f[F_WS];
     a.out2 = f[F_CN];
+    a.q = acc_q ? qf[1] : nullptr;
     a.reduce = 1;
     a.fin = fin(kFinAcc, kAccGrho, gscale);
     if ((e = L_::pw(kPwAdjPre, a, stream)) != cudaSuccess) return cuda_fail(e, "adj pre");
@@ -866,6 +885,8 @@ struct Engine : EngineBase {
       ga.u1 = f[F_X];
       ga.w = f[F_WS];
       ga.kappa = f[F_KAPPA1];
+      ga.q = acc_q ? qf[0] : nullptr;
+      ga.qscale = hprm->s;
       ga.axis = axis;
       ga.g = g;
       ga.twA = twA[lidx(g.n[axis])];
@@ -880,23 +901,31 @@ struct Engine : EngineBase {
     b.prev = f[F_CN];
     b.prev_is_state = 1;
     b.out0 = f[F_ALPHA];
+    b.q = acc_q ? qf[1] : nullptr;
     b.reduce = 1;
     b.fin = fin(kFinAcc, kAccGrho, gscale);
     if ((e = L_::pw(kPwAdjPost, b, stream)) != cudaSuccess) return cuda_fail(e, "adj post");
     return RD_OK;
   }
 
-  // reverse sweep from alpha(1) in F_ALPHA; g_kf, g_rho into acc, g_p into gp
-  rd_status run_adjoint() {
+  // reverse sweep from alpha(1) in F_ALPHA; g_kf, g_rho into acc, g_p into
+  // gp; with acc_q also the per-voxel integrands into the coupling fields
+  rd_status run_adjoint(bool acc_q = false) {
     cudaError_t e;
     rd_status rs;
     hprm->acc[kAccGk] = hprm->acc[kAccGrho] = 0.0;
     // zero the two gradient accumulators on the device without touching the rest
     if ((e = cudaMemsetAsync(&prm->acc[kAccGk], 0, 2 * sizeof(double), stream)) != cudaSuccess)
       return cuda_fail(e, "zero acc");
+    acc_q = acc_q && cfg.coupling;
+    if (acc_q) {
+      have_q = false;
+      for (int i = 0; i < kCouplingFields; ++i)
+        if ((e = cudaMemsetAsync(qf[i], 0, sizeof(T) * nn, stream)) != cudaSuccess) return cuda_fail(e, "zero q");
+    }
     if (!stride) {
       for (int n = cfg.nt - 1; n >= 0; --n)
-        if ((rs = adj_step(n)) != RD_OK) return rs;
+        if ((rs = adj_step(n, acc_q)) != RD_OK) return rs;
     } else {
       for (int k = nseg - 1; k >= 0; --k) {
         if (seg_loaded != k) {
@@ -905,7 +934,7 @@ struct Engine : EngineBase {
         }
         const int n0 = k * stride, n1 = std::min(cfg.nt, n0 + stride);
         for (int n = n1 - 1; n >= n0; --n)
-          if ((rs = adj_step(n)) != RD_OK) return rs;
+          if ((rs = adj_step(n, acc_q)) != RD_OK) return rs;
       }
       seg_loaded = -1;
     }
@@ -989,12 +1018,16 @@ struct Engine : EngineBase {
     a.nn = nn;
     a.fin = fin(kFinSet, 0, 1.0 / double(nn), &prm->kbar1);
     if ((e = L_::coef(a, stream)) != cudaSuccess) return cuda_fail(e, "coefficients");
+    if (cfg.moving_atlas)
+      for (int j = 0; j < 3; ++j)
+        if ((e = L_::from_f64(d[j], anat[j], nn, stream)) != cudaSuccess) return cuda_fail(e, "tissue maps");
     if ((e = cudaMemcpyAsync(&hprm->kbar1, &prm->kbar1, sizeof(double), cudaMemcpyDeviceToHost, stream)) !=
         cudaSuccess)
       return cuda_fail(e, "read kbar");
     if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_fail(e, "sync");
     have_tissue = true;
     have_traj = false;
+    have_q = false;
     return RD_OK;
   }
 
@@ -1019,6 +1052,42 @@ struct Engine : EngineBase {
     return RD_OK;
   }
 
+  rd_status set_anatomy_data(const double* m0, const double* m1, const double* m2) override {
+    if (!cfg.moving_atlas) return fail(RD_ERR_STATE, "rd_set_anatomy_data needs cfg.moving_atlas = 1");
+    if (!have_tissue) return fail(RD_ERR_STATE, "rd_set_tissue is required first");
+    cudaError_t e;
+    const double* src[3] = {m0, m1, m2};
+    for (int j = 0; j < 3; ++j) {
+      const double* dv;
+      if ((e = stage_in(src[j], j, &dv)) != cudaSuccess) return cuda_fail(e, "stage anatomy");
+      if ((e = L_::from_f64(dv, anat[3 + j], nn, stream)) != cudaSuccess) return cuda_fail(e, "convert anatomy");
+    }
+    if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_fail(e, "sync");
+    have_mdata = true;
+    have_q = false;
+    return RD_OK;
+  }
+
+  // q_i = k_f k_w,i Q_k + rho_f rho_w,i Q_rho from the integrands of the
+  // last gradient adjoint
+  rd_status coupling_field(double* q0, double* q1, double* q2) override {
+    if (!cfg.coupling) return fail(RD_ERR_STATE, "rd_coupling_field needs cfg.coupling = 1");
+    if (!have_q) return fail(RD_ERR_STATE, "rd_coupling_field needs a preceding rd_gradient or rd_adjoint");
+    cudaError_t e;
+    double* out[3] = {q0, q1, q2};
+    for (int j = 0; j < 3; ++j) {
+      const double ca = q_kf * cfg.k_w[j], cb = q_rho * cfg.rho_w[j];
+      double* dst = is_device_ptr(out[j]) ? out[j] : stage[0];
+      if ((e = L_::combine(qf[0], qf[1], ca, cb, dst, nn, stream)) != cudaSuccess) return cuda_fail(e, "combine q");
+      if (dst != out[j] &&
+          (e = cudaMemcpyAsync(out[j], dst, sizeof(double) * nn, cudaMemcpyDeviceToHost, stream)) != cudaSuccess)
+        return cuda_fail(e, "q out");
+      // the staging buffer is reused by the next class: finish this copy first
+      if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_fail(e, "sync");
+    }
+    return RD_OK;
+  }
+
   rd_status set_data(const double* d) override {
     cudaError_t e;
     const double* dv;
@@ -1026,6 +1095,7 @@ struct Engine : EngineBase {
     if ((e = L_::from_f64(dv, f[F_D], nn, stream)) != cudaSuccess) return cuda_fail(e, "convert data");
     if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_fail(e, "sync");
     have_data = true;
+    have_q = false;
     return RD_OK;
   }
 
@@ -1047,13 +1117,18 @@ struct Engine : EngineBase {
     if (!have_data) return fail(RD_ERR_STATE, "rd_set_data is required");
     const int it0 = last_iters, so0 = last_solves, gs0 = last_graph_solves;
     begin_call();
-    rd_status s = run_adjoint();
+    rd_status s = run_adjoint(true);
     if (s != RD_OK) return s;
     cudaError_t e;
     if (alpha0_out && (e = field_out(f[F_ALPHA], alpha0_out, 1.0)) != cudaSuccess) return cuda_fail(e, "alpha out");
     last_grad.assign(np + 2, 0.0);
     s = collect(last_grad.data(), theta_p.data());
     if (s == RD_OK) have_grad = true;
+    if ((s == RD_OK || s == RD_ERR_NOCONV) && cfg.coupling) {
+      have_q = true;
+      q_kf = theta_kf;
+      q_rho = theta_rho;
+    }
     s = end_call(s);
     last_iters += it0;
     last_solves += so0;
@@ -1127,7 +1202,7 @@ struct Engine : EngineBase {
     begin_call();
     rd_status rs = run_forward(p, k_f, rho_f);
     if (rs == RD_OK) rs = enqueue_misfit();
-    if (rs == RD_OK) rs = run_adjoint();
+    if (rs == RD_OK) rs = run_adjoint(true);
     if (rs == RD_OK) {
       cudaError_t e = enqueue_results();
       if (e != cudaSuccess) rs = cuda_fail(e, "results");
@@ -1148,6 +1223,11 @@ struct Engine : EngineBase {
     have_traj = true;
     last_grad.assign(grad, grad + np + 2);
     have_grad = true;
+    if (cfg.coupling) {
+      have_q = true;
+      q_kf = hprm_theta_kf;
+      q_rho = hprm_theta_rho;
+    }
     if (hst->sticky == kStTimeout) return fail(RD_ERR_CUDA, "a TMA wait timed out");
     if (hst->sticky == kStNonFinite) return fail(RD_ERR_NONFINITE, "non-finite value in a PCG solve");
     if (hst->sticky == kStNoConv) return fail(RD_ERR_NOCONV, "a PCG solve reached pcg_maxit");
@@ -1305,6 +1385,8 @@ rd_status rd_config_default(rd_config* c) {
   c->rho_w[1] = 0.2;
   c->rho_w[2] = 0.0;
   c->beta_p = 0.0;
+  c->moving_atlas = 0;
+  c->coupling = 0;
   return RD_OK;
 }
 
@@ -1357,6 +1439,11 @@ rd_status rd_set_basis(rd_ctx* c, const double* centers, double sigma) {
 rd_status rd_set_data(rd_ctx* c, const double* d) {
   if (!c || !d) return RD_ERR_ARG;
   return c->e->set_data(d);
+}
+
+rd_status rd_coupling_field(rd_ctx* c, double* q_wm, double* q_gm, double* q_csf) {
+  if (!c || !q_wm || !q_gm || !q_csf) return RD_ERR_ARG;
+  return c->e->coupling_field(q_wm, q_gm, q_csf);
 }
 
 rd_status rd_forward(rd_ctx* c, const double* p, double k_f, double rho_f, double* c1_out, double* misfit) {
@@ -1460,6 +1547,16 @@ struct BatchGraph {
 std::mutex g_batch_mu;
 BatchGraph g_batch;
 }  // namespace
+
+rd_status rd_set_anatomy_data(rd_ctx* c, const double* md_wm, const double* md_gm, const double* md_csf) {
+  if (!c || !md_wm || !md_gm || !md_csf) return RD_ERR_ARG;
+  {
+    // a batch graph captured before holds misfit launches without m_D
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    if (std::find(g_batch.ctxs.begin(), g_batch.ctxs.end(), c) != g_batch.ctxs.end()) g_batch.clear();
+  }
+  return c->e->set_anatomy_data(md_wm, md_gm, md_csf);
+}
 
 rd_status rd_batch_gradient(rd_ctx* const* ctxs, int count, const double* const* p, const double* k_f,
                             const double* rho_f, double* misfit, double* const* grad) {

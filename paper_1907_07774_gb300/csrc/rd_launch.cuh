@@ -43,6 +43,8 @@ struct Launch {
   static cudaError_t phit(const PhiArgs<T>& a, double* out, double scale, cudaStream_t s);
   static cudaError_t from_f64(const double* in, T* out, long long nn, cudaStream_t s);
   static cudaError_t to_f64(const T* in, double* out, long long nn, double scale, cudaStream_t s);
+  static cudaError_t combine(const T* qk, const T* qr, double ca, double cb, double* out, long long nn,
+                             cudaStream_t s);
 };
 
 extern template struct Launch<float>;

@@ -348,4 +348,13 @@ cudaError_t Launch<T>::to_f64(const T* in, double* out, long long nn, double sca
   return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t Launch<T>::combine(const T* qk, const T* qr, double ca, double cb, double* out, long long nn,
+                               cudaStream_t s) {
+  const void* fn = reinterpret_cast<const void*>(k_combine<T>);
+  int grid = detail::grid_for(fn, 0, (nn + kThreads - 1) / kThreads);
+  k_combine<T><<<grid, kThreads, 0, s>>>(qk, qr, ca, cb, out, nn);
+  return cudaGetLastError();
+}
+
 }  // namespace rd

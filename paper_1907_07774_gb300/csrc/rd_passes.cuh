@@ -394,6 +394,8 @@ struct GradArgs {
   const T* u1;   // may be null
   const T* w;
   const T* kappa;
+  T* q;          // optional per-voxel field: q += qscale d_axis(u0 + u1) d_axis(w)
+  double qscale;
   int axis;
   Geom g;
   const cpx<T>* twA;
@@ -440,6 +442,17 @@ __global__ void __launch_bounds__(kThreads) k_grad(GradArgs<T> a) {
         loc += k.x * du[r].x * dw[r].x + k.y * du[r].y * dw[r].y;
       }
       red += double(loc * scale);
+      if (a.q) {
+        const T qs = T(a.qscale) * scale;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const long long off = (long long)idx_a<L>(r, t) * st;
+          cpx<T> qv = ld2<T, CONTIG>(a.q, b0, b1, off);
+          qv.x += qs * du[r].x * dw[r].x;
+          qv.y += qs * du[r].y * dw[r].y;
+          st2<T, CONTIG>(a.q, b0, b1, off, qv);
+        }
+      }
     }
   }
   double vv[1] = {red};
@@ -471,6 +484,9 @@ struct PwArgs {
   const T* d;
   const T* prev;
   const T* rho1;
+  const T* m[3];    // tissue maps (Moving-Atlas misfit), null when unused
+  const T* md[3];   // anatomy data m_D
+  T* q;             // adjoint passes: per-voxel rho_f integrand, null when unused
   T* out0;
   T* out1;
   T* out2;
@@ -507,13 +523,25 @@ __global__ void __launch_bounds__(kThreads) k_pw(PwArgs<T> a) {
       const T c1 = logistic(a.a[i], e);
       const T dd = a.d[i];
       const T r = c1 - dd;
-      red += double(r * r);
-      a.out0[i] = dd - c1;
+      T rr = r * r, al = dd - c1;
+      if (a.md[0]) {
+        // D_m = 1/2 sum_i (m_i (1 - c) - m_D,i)^2 and its -dD_m/dc
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          const T mi = a.m[j][i];
+          const T ej = mi * (T(1) - c1) - a.md[j][i];
+          rr += ej * ej;
+          al += mi * ej;
+        }
+      }
+      red += double(rr);
+      a.out0[i] = al;
       if (a.out1) a.out1[i] = c1;
     } else if (KIND == kPwAdjPre) {
       const T al = a.a[i], css = a.b[i];
       const T cnext = logistic(css, e);
       red += double(al * rho1 * cnext * (T(1) - cnext));
+      if (a.q) a.q[i] -= s * al * cnext * (T(1) - cnext);
       a.out0[i] = logistic_dc(css, e) * al;
       a.out1[i] = logistic(cn, e) + css;
       a.out2[i] = cn;
@@ -522,6 +550,7 @@ __global__ void __launch_bounds__(kThreads) k_pw(PwArgs<T> a) {
       const T ast = a.a[i] + T(2) * a.b[i] + a.d[i];
       const T cs = logistic(c, e);
       red += double(ast * rho1 * cs * (T(1) - cs));
+      if (a.q) a.q[i] -= s * ast * cs * (T(1) - cs);
       a.out0[i] = logistic_dc(c, e) * ast;
     } else if (KIND == kPwTlPre) {
       const T css = a.b[i];
@@ -535,7 +564,12 @@ __global__ void __launch_bounds__(kThreads) k_pw(PwArgs<T> a) {
       const T cnext = logistic(css, e);
       a.out0[i] = logistic_dc(css, e) * chss + v_rho * s * rho1 * cnext * (T(1) - cnext);
     } else if (KIND == kPwNeg) {
-      a.out0[i] = -a.a[i];
+      T w = T(1);
+      if (a.md[0]) {
+#pragma unroll
+        for (int j = 0; j < 3; ++j) w += a.m[j][i] * a.m[j][i];
+      }
+      a.out0[i] = -w * a.a[i];
     } else if (KIND == kPwState) {
       a.out0[i] = cn;
     }
@@ -574,6 +608,15 @@ __global__ void __launch_bounds__(kThreads) k_coef(CoefArgs<T> a) {
   }
   double vv[1] = {red};
   reduce_finish<1>(vv, a.fin);
+}
+
+// out = ca qk + cb qr in FP64 (coupling field of one tissue class)
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_combine(const T* __restrict__ qk, const T* __restrict__ qr,
+                                                      double ca, double cb, double* __restrict__ out,
+                                                      long long nn) {
+  for (long long i = (long long)blockIdx.x * kThreads + threadIdx.x; i < nn; i += (long long)gridDim.x * kThreads)
+    out[i] = ca * double(qk[i]) + cb * double(qr[i]);
 }
 
 template <typename TO, typename TI>

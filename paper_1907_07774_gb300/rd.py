@@ -29,7 +29,8 @@ class rd_config(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int * 3), ("nt", ctypes.c_int), ("t_end", ctypes.c_double),
                 ("prec", ctypes.c_int), ("pcg_rtol", ctypes.c_double), ("pcg_maxit", ctypes.c_int),
                 ("ckpt_stride", ctypes.c_int), ("k_w", ctypes.c_double * 3),
-                ("rho_w", ctypes.c_double * 3), ("beta_p", ctypes.c_double)]
+                ("rho_w", ctypes.c_double * 3), ("beta_p", ctypes.c_double), ("moving_atlas", ctypes.c_int),
+                ("coupling", ctypes.c_int)]
 
 
 _lib = None
@@ -51,6 +52,8 @@ def lib():
         "rd_set_tissue": ([vp, vp, vp, vp], st),
         "rd_set_basis": ([vp, vp, cd], st),
         "rd_set_data": ([vp, vp], st),
+        "rd_set_anatomy_data": ([vp, vp, vp, vp], st),
+        "rd_coupling_field": ([vp, vp, vp, vp], st),
         "rd_forward": ([vp, vp, cd, cd, vp, _c_double_p], st),
         "rd_adjoint": ([vp, vp], st),
         "rd_gradient": ([vp, vp, cd, cd, _c_double_p, vp], st),
@@ -139,7 +142,7 @@ class Context:
 
     def __init__(self, n, nt, np_, prec="fp64", pcg_rtol=None, pcg_maxit=200, ckpt_stride=0,
                  k_w=(1.0, 0.1, 0.0), rho_w=(1.0, 0.2, 0.0), beta_p=0.0, t_end=1.0,
-                 stream=None, device=None):
+                 stream=None, device=None, moving_atlas=False, coupling=False):
         import torch
         L = lib()
         cfg = rd_config()
@@ -157,6 +160,8 @@ class Context:
             cfg.k_w[a] = float(k_w[a])
             cfg.rho_w[a] = float(rho_w[a])
         cfg.beta_p = float(beta_p)
+        cfg.moving_atlas = 1 if moving_atlas else 0
+        cfg.coupling = 1 if coupling else 0
         self.cfg = cfg
         self.n = n
         self.np = int(np_)
@@ -207,6 +212,19 @@ class Context:
     def rd_set_data(self, d):
         a, k = _ptr(d)
         self._call(lib().rd_set_data(self.h, a))
+
+    def rd_coupling_field(self, q_wm=None, q_gm=None, q_csf=None):
+        """Coupling field q of the last gradient; fills the given FP64
+        buffers (host arrays or CUDA tensors) or returns three new arrays."""
+        if q_wm is None:
+            q_wm, q_gm, q_csf = (np.zeros(self.n) for _ in range(3))
+        (a, ka), (b, kb), (c, kc) = _ptr(q_wm), _ptr(q_gm), _ptr(q_csf)
+        self._call(lib().rd_coupling_field(self.h, a, b, c))
+        return q_wm, q_gm, q_csf
+
+    def rd_set_anatomy_data(self, md_wm, md_gm, md_csf):
+        (a, ka), (b, kb), (c, kc) = _ptr(md_wm), _ptr(md_gm), _ptr(md_csf)
+        self._call(lib().rd_set_anatomy_data(self.h, a, b, c))
 
     # -- solves -------------------------------------------------------------
     def rd_forward(self, p, k_f, rho_f, c1_out=None, allow_noconv=False):

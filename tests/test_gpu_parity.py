@@ -186,6 +186,131 @@ def test_beta_p_regularisation_terms():
     assert abs(J - J_or) <= 1e-10 * J_or and rel(g, g_or) <= 1e-10
 
 
+def _anatomy_data(prob, seed=41):
+    rng = np.random.default_rng(seed)
+    return [np.clip(mi + 0.1 * rng.standard_normal(prob.n), 0, 1) * (mi > 0)
+            for mi in (prob.m_wm, prob.m_gm, prob.m_csf)]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_moving_atlas_gradient_and_hessvec_match_oracle(prec):
+    """Objective D_c + D_m: misfit, adjoint final condition, alpha(0),
+    gradient and the 1 + sum m_i^2 weighted Gauss-Newton product."""
+    prob, M, d = _grad_case()
+    md = _anatomy_data(prob)
+    M.set_anatomy_data(md)
+    J_or, g_or, _, a0_or = M.gradient(prob.p, prob.k_f, prob.rho_f, d)
+    v = synth.random_directions(1, len(prob.p) + 2, 21)[0]
+    hv_or = M.hessvec(prob.p, prob.k_f, prob.rho_f, v)
+    ctx = gpu_for(prob, prec, moving_atlas=True)
+    ctx.rd_set_data(d)
+    J0, g0 = ctx.rd_gradient(prob.p, prob.k_f, prob.rho_f)      # before m_D: tumor misfit only
+    ctx.rd_set_anatomy_data(*md)
+    J, g = ctx.rd_gradient(prob.p, prob.k_f, prob.rho_f)
+    assert J > J0
+    assert abs(J - J_or) <= TOL[prec] * abs(J_or)
+    assert rel(g, g_or) <= TOL[prec]
+    a0 = np.zeros(prob.n)
+    ctx.rd_forward(prob.p, prob.k_f, prob.rho_f)
+    ctx.rd_adjoint(a0)
+    assert rel(a0, a0_or) <= TOL[prec]
+    hv = ctx.rd_hessvec(prob.p, prob.k_f, prob.rho_f, v)
+    assert rel(hv, hv_or) <= TOL[prec]
+
+
+def test_moving_atlas_needs_its_config_flag():
+    prob, M, d = _grad_case()
+    ctx = gpu_for(prob, "fp64")
+    with pytest.raises(RuntimeError):
+        ctx.rd_set_anatomy_data(*_anatomy_data(prob))
+
+
+def test_batch_graph_sees_anatomy_data_set_after_capture():
+    prob, M, d = _grad_case()
+    md = _anatomy_data(prob)
+    ctxs = [gpu_for(prob, "mixed", moving_atlas=True) for _ in range(2)]
+    for c in ctxs:
+        c.rd_set_data(d)
+    th = [(prob.p, prob.k_f, prob.rho_f)] * 2
+    J0, _ = R.rd_batch_gradient(ctxs, th)
+    ctxs[1].rd_set_anatomy_data(*md)
+    J1, g1 = R.rd_batch_gradient(ctxs, th)
+    Js, gs = ctxs[1].rd_gradient(prob.p, prob.k_f, prob.rho_f)
+    assert J1[0] == J0[0] and J1[1] > J0[1]
+    assert J1[1] == Js and np.array_equal(g1[1], gs)
+
+
+KW3, RW3 = (1.0, 0.1, 0.3), (1.0, 0.2, 0.05)   # every tissue class weighted
+
+
+def _coupling_case(nt=4):
+    prob, _, d = _grad_case(nt=nt)
+    M = orc.Model(prob.n, prob.m_wm, prob.m_gm, prob.m_csf, prob.centers, prob.sigma, prob.nt,
+                  k_w=KW3, rho_w=RW3, rtol=1e-13, maxit=1000, kind="numpy")
+    return prob, M, d
+
+
+def _coupling_ctx(prob, prec, **kw):
+    ctx = R.Context(prob.n, prob.nt, len(prob.p), prec=prec, pcg_rtol=RTOL[prec], pcg_maxit=1000,
+                    k_w=KW3, rho_w=RW3, coupling=True, **kw)
+    ctx.rd_set_tissue(prob.m_wm, prob.m_gm, prob.m_csf)
+    ctx.rd_set_basis(prob.centers, prob.sigma)
+    return ctx
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_coupling_field_matches_oracle(prec):
+    prob, M, d = _coupling_case()
+    q_or = M.coupling(prob.p, prob.k_f, prob.rho_f, d)
+    ctx = _coupling_ctx(prob, prec)
+    ctx.rd_set_data(d)
+    with pytest.raises(RuntimeError):
+        ctx.rd_coupling_field()                       # no gradient yet
+    ctx.rd_gradient(prob.p, prob.k_f, prob.rho_f)
+    q = ctx.rd_coupling_field()
+    for i in range(3):
+        assert rel(q[i], q_or[i]) <= TOL[prec], i
+    # a Hessian-vector product at the same parameters leaves q alone
+    v = synth.random_directions(1, len(prob.p) + 2, 22)[0]
+    ctx.rd_hessvec(prob.p, prob.k_f, prob.rho_f, v)
+    q2 = ctx.rd_coupling_field()
+    assert all(np.array_equal(a, b) for a, b in zip(q, q2))
+    # device outputs
+    qd = [torch.zeros(prob.n, dtype=torch.float64, device="cuda") for _ in range(3)]
+    ctx.rd_coupling_field(*qd)
+    assert all(np.array_equal(a, b.cpu().numpy()) for a, b in zip(q, qd))
+    # a new forward solve invalidates it
+    ctx.rd_forward(prob.p, 1.1 * prob.k_f, prob.rho_f)
+    with pytest.raises(RuntimeError):
+        ctx.rd_coupling_field()
+
+
+def test_coupling_field_needs_its_config_flag():
+    prob, M, d = _grad_case()
+    ctx = gpu_for(prob, "fp64")
+    ctx.rd_set_data(d)
+    ctx.rd_gradient(prob.p, prob.k_f, prob.rho_f)
+    with pytest.raises(RuntimeError):
+        ctx.rd_coupling_field()
+
+
+def test_coupling_field_checkpointed_and_batched_are_bitwise_identical():
+    prob, M, d = _coupling_case(nt=8)
+    out = []
+    for stride in (0, 3):
+        ctx = _coupling_ctx(prob, "mixed", ckpt_stride=stride)
+        ctx.rd_set_data(d)
+        ctx.rd_gradient(prob.p, prob.k_f, prob.rho_f)
+        out.append(ctx.rd_coupling_field())
+    ctxs = [_coupling_ctx(prob, "mixed") for _ in range(2)]
+    for c in ctxs:
+        c.rd_set_data(d)
+    R.rd_batch_gradient(ctxs, [(prob.p, prob.k_f, prob.rho_f), (prob.p, 0.5 * prob.k_f, prob.rho_f)])
+    out.append(ctxs[0].rd_coupling_field())
+    for q in out[1:]:
+        assert all(np.array_equal(a, b) for a, b in zip(out[0], q))
+
+
 # ------------------------------------------------------- paper workloads
 def test_forward_problem_64_fp64_matches_oracle():
     """64^3, nt = 16 forward recipe (8 Gaussians, sigma = 2 pi / 64)."""

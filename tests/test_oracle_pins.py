@@ -294,3 +294,124 @@ def test_misfit_quadrature_weight():
     c = np.full(prob.n, 0.5)
     d = np.zeros(prob.n)
     assert abs(M.misfit(c, d, np.zeros(8)) - 0.5 * 0.25 * (TWO_PI ** 3)) < 1e-12
+
+
+@pytest.fixture(scope="module")
+def moving_atlas_problem(small_problem):
+    M, prob, d, th = small_problem
+    import copy
+    Mm = copy.copy(M)
+    rng = np.random.default_rng(41)
+    Mm.set_anatomy_data([np.clip(mi + 0.1 * rng.standard_normal(prob.n), 0, 1) * (mi > 0) for mi in Mm.m])
+    return Mm, prob, d, th
+
+
+def test_moving_atlas_gradient_matches_central_differences(moving_atlas_problem):
+    """D_c + D_m objective: the extra final condition m^T (m (1 - c) - m_D)."""
+    M, prob, d, th = moving_atlas_problem
+    J, g, _, _ = M.gradient(th[:-2], th[-2], th[-1], d)
+    J0 = _J(M, d, th)
+    assert abs(J - J0) < 1e-14 * J0
+    for v in list(synth.random_directions(2, len(th), 42)) + [np.eye(len(th))[-2]]:
+        eps = 1e-6
+        fd = (_J(M, d, th + eps * v) - _J(M, d, th - eps * v)) / (2 * eps)
+        assert abs(fd - g @ v) <= 1e-6 * max(abs(fd), 1e-3 * np.linalg.norm(g))
+
+
+def test_moving_atlas_term_changes_objective_and_hessian(moving_atlas_problem, small_problem):
+    M, prob, d, th = moving_atlas_problem
+    M0 = small_problem[0]
+    assert _J(M, d, th) > _J(M0, d, th)
+    c1, _ = M.forward(th[:-2], th[-2], th[-1])
+    d0 = c1.copy()
+    # with zero tumor residual the remaining D_m residual keeps the GN Hessian
+    # symmetric positive: check symmetry with the weight 1 + sum m_i^2
+    v, w = synth.random_directions(2, len(th), 43)
+    hv = M.hessvec(th[:-2], th[-2], th[-1], v)
+    hw = M.hessvec(th[:-2], th[-2], th[-1], w)
+    assert abs(v @ hw - w @ hv) < 1e-10 * abs(v @ hw) and v @ hv > 0
+
+
+def test_moving_atlas_gauss_newton_hessian_is_exact_at_zero_residual(small_problem):
+    """With d = c(1) and m_D = m (1 - c(1)) both residuals vanish, so the
+    Gauss-Newton Hessian equals the true Hessian: H v must match central
+    differences of the reduced gradient, which fixes the final weight
+    1 + sum_i m_i^2 of the tangent c(1)."""
+    import copy
+    M0, prob, _, th = small_problem
+    M = copy.copy(M0)
+    c1, _ = M.forward(th[:-2], th[-2], th[-1])
+    M.set_anatomy_data([mi * (1.0 - c1) for mi in M.m])
+    d = c1.copy()
+    v = synth.random_directions(1, len(th), 44)[0]
+    hv = M.hessvec(th[:-2], th[-2], th[-1], v)
+    eps = 1e-5
+    gp = M.gradient(*(lambda t: (t[:-2], t[-2], t[-1]))(th + eps * v), d)[1]
+    gm = M.gradient(*(lambda t: (t[:-2], t[-2], t[-1]))(th - eps * v), d)[1]
+    fd = (gp - gm) / (2 * eps)
+    assert np.linalg.norm(fd - hv) <= 1e-5 * np.linalg.norm(hv)
+    # the plain tumor weight would miss the anatomy term
+    M1 = copy.copy(M0)
+    hv1 = M1.hessvec(th[:-2], th[-2], th[-1], v)
+    assert np.linalg.norm(fd - hv1) > 1e-2 * np.linalg.norm(hv)
+
+
+def _tissue_perturbation(n, seed):
+    """Smooth seeded field: a few random periodic Gaussians."""
+    rng = np.random.default_rng(seed)
+    x = synth.grid_coords(n)
+    out = np.zeros(n)
+    for _ in range(3):
+        c = rng.uniform(0, TWO_PI, 3)
+        r2 = 0.0
+        for a in range(3):
+            dx = np.abs(x[a] - c[a])
+            dx = np.minimum(dx, TWO_PI - dx)
+            shape = [1, 1, 1]
+            shape[a] = n[a]
+            r2 = r2 + (dx ** 2).reshape(shape)
+        out += rng.standard_normal() * np.exp(-r2 / (2 * 0.8 ** 2))
+    return out
+
+
+def test_coupling_field_is_the_derivative_through_the_coefficients(small_problem):
+    """q(x) of the Picard step (Sec. 2.2): perturbing tissue class i inside
+    the coefficients k and f only (Eq. coeff_tumor) by eps dm must change the
+    objective by eps h^3 sum_x q_i dm at first order.  Checked per class, so a
+    swapped weight index, a dropped diffusion or reaction term or a wrong sign
+    each fails."""
+    M, prob, d, th = small_problem
+    p, k_f, rho_f = th[:-2], th[-2], th[-1]
+    ms = [prob.m_wm, prob.m_gm, prob.m_csf]
+
+    def J_with(i, dm):
+        mm = [m.copy() for m in ms]
+        mm[i] = mm[i] + dm
+        Mi = rd.Model(prob.n, *mm, prob.centers, prob.sigma, prob.nt, k_w=(1.0, 0.1, 0.3),
+                      rho_w=(1.0, 0.2, 0.05), kind="numpy", rtol=1e-13)
+        c1, _ = Mi.forward(p, k_f, rho_f)
+        return Mi.misfit(c1, d, p)
+
+    # non-zero CSF weights so every class is exercised
+    M3 = rd.Model(prob.n, *ms, prob.centers, prob.sigma, prob.nt, k_w=(1.0, 0.1, 0.3),
+                  rho_w=(1.0, 0.2, 0.05), kind="numpy", rtol=1e-13)
+    q = M3.coupling(p, k_f, rho_f, d)
+    eps = 1e-4
+    for i in range(3):
+        dm = _tissue_perturbation(prob.n, 60 + i)
+        fd = (J_with(i, eps * dm) - J_with(i, -eps * dm)) / (2 * eps)
+        lin = M3.h3 * float(np.sum(q[i] * dm))
+        assert abs(fd - lin) <= 1e-6 * abs(lin), (i, fd, lin)
+
+
+def test_coupling_field_euler_identity(small_problem):
+    """k and f are linear in m, so h^3 sum_x sum_i m_i q_i equals
+    k_f dJ/dk_f + rho_f dJ/drho_f; with zero CSF weights q_CSF vanishes."""
+    M, prob, d, th = small_problem
+    p, k_f, rho_f = th[:-2], th[-2], th[-1]
+    q = M.coupling(p, k_f, rho_f, d)
+    _, g, _, _ = M.gradient(p, k_f, rho_f, d)
+    lhs = M.h3 * sum(float(np.sum(mi * qi)) for mi, qi in zip(M.m, q))
+    rhs = k_f * g[-2] + rho_f * g[-1]
+    assert abs(lhs - rhs) <= 1e-12 * abs(rhs)
+    assert np.all(q[2] == 0.0)
