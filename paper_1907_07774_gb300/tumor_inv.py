@@ -25,6 +25,13 @@ Readings where the paper leaves room:
   Hoyer sparsity >= target lowers beta, a denser one raises it; the zero
   vector counts as too sparse.  The result is the smallest tried beta whose
   solution is non-zero and sparse enough.
+* ``p >= 0`` (default ``nonneg=True``): with positive Gaussians, c(0) = Phi p
+  is a concentration only for non-negative p, and a negative c(0) drives the
+  exact logistic step towards its singular denominator.  The l1 prox is then
+  the one-sided threshold ``max(0, x - alpha beta)``.
+* A trial point whose solve fails with a non-finite value is treated as a
+  failed trial: GIST halves alpha, L-BFGS restarts the line search from a
+  ten times shorter step.
 * l2 phase: the bound ``k_f >= 0`` caps the line-search step (``stpmax``);
   on the bound, k_f is held fixed while its gradient points outward, and
   convergence is measured on the projected gradient.
@@ -38,9 +45,45 @@ from dataclasses import dataclass, field
 import numpy as np
 
 
+class NonFiniteTrial(Exception):
+    """A trial point whose state or adjoint solve produced a non-finite value."""
+
+
+def _is_nonfinite_error(exc):
+    # the library reports RD_ERR_NONFINITE (6) through RDError.status
+    return getattr(exc, "status", None) == 6
+
+
+def _forward(solver, p, k_f, rho_f):
+    try:
+        J = solver.rd_forward(p, k_f, rho_f)
+    except Exception as exc:
+        if _is_nonfinite_error(exc):
+            return math.inf
+        raise
+    return J if np.isfinite(J) else math.inf
+
+
+def _gradient(solver, p, k_f, rho_f):
+    try:
+        J, g = solver.rd_gradient(p, k_f, rho_f)
+    except Exception as exc:
+        if _is_nonfinite_error(exc):
+            raise NonFiniteTrial() from exc
+        raise
+    g = np.asarray(g, dtype=np.float64)
+    if not (np.isfinite(J) and np.all(np.isfinite(g))):
+        raise NonFiniteTrial()
+    return J, g
+
+
 # ------------------------------------------------------------------ l1 phase
-def soft_threshold(x, t):
-    """``sign(x) max(0, |x| - t)`` elementwise (the closed form of Sec. 3.1)."""
+def soft_threshold(x, t, nonneg=False):
+    """``sign(x) max(0, |x| - t)`` elementwise (the closed form of Sec. 3.1);
+    with ``nonneg`` the prox of ``t |.|`` plus the constraint ``>= 0``,
+    ``max(0, x - t)``."""
+    if nonneg:
+        return np.maximum(0.0, x - t)
     return np.sign(x) * np.maximum(0.0, np.abs(x) - t)
 
 
@@ -78,7 +121,7 @@ class GistResult:
 
 
 def gist(solver, p0, k_f, rho_f, beta, alpha0=1.0, sigma=1e-5, tau_j=1e-4, maxit=50,
-         max_backtracks=60, alpha_min=1e-30, alpha_max=1e10):
+         max_backtracks=60, alpha_min=1e-30, alpha_max=1e10, nonneg=True):
     """GIST (Sec. 3.1) on ``F(p) = D(p) + beta ||p||_1`` at fixed k_f, rho_f.
 
     Each iteration takes a gradient step of length alpha on D, applies the
@@ -86,8 +129,10 @@ def gist(solver, p0, k_f, rho_f, beta, alpha0=1.0, sigma=1e-5, tau_j=1e-4, maxit
     condition holds, and proposes the next alpha by Barzilai-Borwein."""
     npar = solver.np
     p = np.asarray(p0, dtype=np.float64).copy()
-    D, g = solver.rd_gradient(p, k_f, rho_f)
-    g = np.asarray(g[:npar], dtype=np.float64)
+    if nonneg:
+        p = np.maximum(p, 0.0)
+    D, g = _gradient(solver, p, k_f, rho_f)
+    g = g[:npar]
     F = D + beta * float(np.sum(np.abs(p)))
     F0 = F
     alpha = float(alpha0)
@@ -98,8 +143,8 @@ def gist(solver, p0, k_f, rho_f, beta, alpha0=1.0, sigma=1e-5, tau_j=1e-4, maxit
     for it in range(1, maxit + 1):
         accepted = False
         for _ in range(max_backtracks):
-            p_new = soft_threshold(p - alpha * g, alpha * beta)
-            D_new = solver.rd_forward(p_new, k_f, rho_f)
+            p_new = soft_threshold(p - alpha * g, alpha * beta, nonneg)
+            D_new = _forward(solver, p_new, k_f, rho_f)
             evals += 1
             F_new = D_new + beta * float(np.sum(np.abs(p_new)))
             dp = p_new - p
@@ -144,8 +189,8 @@ def beta_search(solver, p0, k_f, rho_f, target=0.95, steps=6, beta_max=None, **g
     npar = solver.np
     p0 = np.asarray(p0, dtype=np.float64)
     if beta_max is None:
-        _, g0 = solver.rd_gradient(p0, k_f, rho_f)
-        beta_max = float(np.max(np.abs(np.asarray(g0[:npar]))))
+        _, g0 = _gradient(solver, p0, k_f, rho_f)
+        beta_max = float(np.max(np.abs(g0[:npar])))
     lo, hi = 0.0, float(beta_max)
     beta = hi
     best = None
@@ -427,7 +472,18 @@ def lbfgs(fg, x0, m=10, maxit=100, gtol_rel=1e-5, g_ref=None, lower=None, ls_kw=
             cache[a] = (xa, fa, ga)
             return fa, float(ga @ d)
 
-        ls = more_thuente(phi, f, slope, stp=min(stp0, stpmax), stpmin=0.0, stpmax=stpmax, **ls_kw)
+        ls = None
+        stp_try = min(stp0, stpmax)
+        for _ in range(12):
+            try:
+                ls = more_thuente(phi, f, slope, stp=stp_try, stpmin=0.0, stpmax=stpmax, **ls_kw)
+                break
+            except NonFiniteTrial:
+                evals += 1
+                stp_try *= 0.1
+                stpmax = stp_try      # never step back into the failing region
+        if ls is None:
+            break
         evals += ls.evals
         x_new, f_new, g_new = cache[ls.stp]
         if not f_new < f:
@@ -463,7 +519,7 @@ class TumorInversionResult:
 
 
 def weighted_l2(solver, p0, k_f0, rho_f, beta, weights, invert_rho=False, k_f_scale=None,
-                rho_scale=None, opttol=1e-3, maxit=50, m=10, g_ref=None, callback=None):
+                rho_scale=None, opttol=1e-3, maxit=50, m=10, g_ref=None, callback=None, nonneg=True):
     """Weighted-l2 phase: L-BFGS + More-Thuente on
     ``D(p, k_f) + beta / 2 sum_i w_i p_i^2`` (Sec. 2.3, Sec. 3.1), k_f >= 0,
     optionally also rho_f.  Variables are scaled (k_f by ``k_f_scale``,
@@ -486,8 +542,7 @@ def weighted_l2(solver, p0, k_f0, rho_f, beta, weights, invert_rho=False, k_f_sc
 
     def fg(x):
         p, kf, rf = unpack(x)
-        J, g = solver.rd_gradient(p, max(kf, 0.0), rf)
-        g = np.asarray(g, dtype=np.float64)
+        J, g = _gradient(solver, p, max(kf, 0.0), rf)
         J = J + 0.5 * beta * float(np.sum(w * p * p))
         gx = np.empty(nv)
         gx[:npar] = g[:npar] + beta * w * p
@@ -503,22 +558,25 @@ def weighted_l2(solver, p0, k_f0, rho_f, beta, weights, invert_rho=False, k_f_sc
         g_ref = fg(xr)[1]
     lower = np.full(nv, -np.inf)
     lower[npar] = 0.0
+    if nonneg:
+        lower[:npar] = 0.0
     return lbfgs(fg, x0, m=m, maxit=maxit, gtol_rel=opttol, g_ref=g_ref, lower=lower, callback=callback), scale
 
 
 def tumor_inversion(solver, rho_f, k_f_l2=None, p0=None, target=0.95, beta_steps=6, gist_kw=None,
                     tau_s=0.1, w_large=1.0, w_small=0.0, beta_l2=1e-4, opttol=1e-3, l2_maxit=50,
-                    invert_rho=False):
+                    invert_rho=False, nonneg=True):
     """Both phases (Sec. 2.3): l1 with k_f = 0 and the Hoyer beta search,
     then weighted l2 on (p, k_f) from the l1 solution; ``k_f_l2`` is the
     starting diffusivity of the l2 phase (default 0)."""
     npar = solver.np
     p0 = np.zeros(npar) if p0 is None else np.asarray(p0, dtype=np.float64)
-    l1 = beta_search(solver, p0, 0.0, rho_f, target=target, steps=beta_steps, **(gist_kw or {}))
+    l1 = beta_search(solver, p0, 0.0, rho_f, target=target, steps=beta_steps,
+                     **dict({"nonneg": nonneg}, **(gist_kw or {})))
     w = l2_weights(l1.p, tau_s, w_large, w_small)
     kf0 = 0.0 if k_f_l2 is None else float(k_f_l2)
     l2, scale = weighted_l2(solver, l1.p, kf0, rho_f, beta_l2, w, invert_rho=invert_rho, opttol=opttol,
-                            maxit=l2_maxit)
+                            maxit=l2_maxit, nonneg=nonneg)
     th = l2.x * scale
     rf = th[npar + 1] if invert_rho else rho_f
     return TumorInversionResult(p=th[:npar], k_f=max(th[npar], 0.0), rho_f=rf, misfit=l2.f, beta_l1=l1.beta,

@@ -92,7 +92,7 @@ def test_gist_reaches_the_lasso_optimum():
     G, b, _ = _sparse_problem()
     s = FakeSolver(G, b)
     beta = 0.05
-    r = T.gist(s, np.zeros(s.np), 0.0, 0.0, beta, tau_j=1e-22, maxit=5000)
+    r = T.gist(s, np.zeros(s.np), 0.0, 0.0, beta, tau_j=1e-22, maxit=5000, nonneg=False)
     _, g = s.rd_gradient(r.p, 0.0, 0.0)
     g = g[:s.np]
     on = r.p != 0.0
@@ -101,6 +101,23 @@ def test_gist_reaches_the_lasso_optimum():
     assert np.max(np.abs(g[~on])) <= beta * (1 + 1e-6)
     objs = [h["objective"] for h in r.history]
     assert all(b_ <= a_ + 1e-15 for a_, b_ in zip(objs, objs[1:]))
+
+
+def test_gist_nonnegative_reaches_its_optimality_conditions():
+    """min 1/2 |G p - b|^2 + beta |p|_1 s.t. p >= 0:
+    g_i = -beta where p_i > 0, g_i >= -beta where p_i = 0."""
+    G, b, _ = _sparse_problem(seed=12)
+    s = FakeSolver(G, b)
+    beta = 0.02
+    r = T.gist(s, np.zeros(s.np), 0.0, 0.0, beta, tau_j=1e-22, maxit=5000)
+    assert np.all(r.p >= 0.0)
+    _, g = s.rd_gradient(r.p, 0.0, 0.0)
+    g = g[:s.np]
+    on = r.p > 0.0
+    assert on.any()
+    assert np.max(np.abs(g[on] + beta)) <= 1e-6
+    assert np.min(g[~on]) >= -beta * (1 + 1e-6)
+    assert np.array_equal(T.soft_threshold(np.array([-2.0, 0.5, 3.0]), 1.0, nonneg=True), [0.0, 0.0, 2.0])
 
 
 def test_gist_with_beta_above_the_gradient_bound_stays_at_zero():
@@ -116,7 +133,7 @@ def test_beta_search_finds_a_sparse_solution_and_brackets_the_target():
     G, b, x = _sparse_problem(m=80, n=60, k=2, seed=4, noise=0.05)
     s = FakeSolver(G, b)
     res = T.beta_search(s, np.zeros(s.np), 0.0, 0.0, target=0.95, steps=10,
-                        tau_j=1e-16, maxit=2000)
+                        tau_j=1e-16, maxit=2000, nonneg=False)
     assert np.any(res.p) and res.sparsity >= 0.95
     sparse = [t["beta"] for t in res.tried if t["nnz"] > 0 and t["sparsity"] >= 0.95]
     assert res.beta == min(sparse)
@@ -234,7 +251,7 @@ def test_weighted_l2_phase_reaches_the_ridge_solution():
     s = FakeSolver(G, b, u=u)
     w = T.l2_weights(x, 0.1, 10.0, 0.1)
     beta = 0.02
-    res, scale = T.weighted_l2(s, np.zeros(12), 0.05, 0.0, beta, w, opttol=1e-10, maxit=400)
+    res, scale = T.weighted_l2(s, np.zeros(12), 0.05, 0.0, beta, w, opttol=1e-10, maxit=400, nonneg=False)
     th = res.x * scale
     M = np.column_stack([G, u])
     reg = np.diag(np.concatenate([beta * w, [0.0]]))
@@ -247,7 +264,8 @@ def test_weighted_l2_keeps_k_f_nonnegative():
     G, b, _ = _sparse_problem(m=40, n=10, k=2, seed=8)
     u = np.random.default_rng(9).standard_normal(40)
     s = FakeSolver(G, b - 0.5 * u, u=u)        # the unconstrained k_f would be -0.5
-    res, scale = T.weighted_l2(s, np.zeros(10), 0.1, 0.0, 1e-3, np.ones(10), opttol=1e-8, maxit=200)
+    res, scale = T.weighted_l2(s, np.zeros(10), 0.1, 0.0, 1e-3, np.ones(10), opttol=1e-8, maxit=200,
+                               nonneg=False)
     th = res.x * scale
     assert res.converged
     assert th[10] == 0.0 and res.g[10] > 0.0
@@ -263,9 +281,56 @@ def test_tumor_inversion_runs_both_phases():
     v = 0.1 * rng.standard_normal(80)
     s = FakeSolver(G, b + 0.2 * u + 0.04 * v, u=u, v=v)
     out = T.tumor_inversion(s, rho_f=0.0, k_f_l2=0.05, beta_steps=8, gist_kw={"tau_j": 1e-14, "maxit": 500},
-                            tau_s=0.1, w_large=1.0, w_small=0.0, beta_l2=1e-3, opttol=1e-6, l2_maxit=300)
+                            tau_s=0.1, w_large=1.0, w_small=0.0, beta_l2=1e-3, opttol=1e-6, l2_maxit=300,
+                            nonneg=False)
     assert out.sparsity >= 0.95
     assert out.l2.converged and out.k_f >= 0.0
     J0 = s.rd_forward(out.l1.p, 0.0, 0.0)
     assert out.misfit < J0
     assert abs(out.k_f - 0.2) < 0.1
+
+
+class _NonFinite(RuntimeError):
+    status = 6
+
+
+class BlowUpSolver(FakeSolver):
+    """Fails like the library's RD_ERR_NONFINITE beyond k_f = 0.4."""
+
+    def rd_forward(self, p, k_f, rho_f):
+        if k_f > 0.4:
+            raise _NonFinite("non-finite value in a PCG solve")
+        return super().rd_forward(p, k_f, rho_f)
+
+
+def test_nonfinite_trials_shorten_the_step_instead_of_failing():
+    G, b, _ = _sparse_problem(m=40, n=8, k=2, seed=13)
+    u = np.random.default_rng(14).standard_normal(40)
+    s = BlowUpSolver(G, b + 0.3 * u, u=u)
+    res, scale = T.weighted_l2(s, np.zeros(8), 0.01, 0.0, 1e-4, np.ones(8), opttol=1e-8, maxit=300,
+                               k_f_scale=1.0, nonneg=False)
+    th = res.x * scale
+    assert res.converged and abs(th[8] - 0.3) < 0.05
+    # GIST treats a failing trial as a rejected step and halves alpha
+    class BigP(FakeSolver):
+        def rd_forward(self, p, k_f, rho_f):
+            if np.max(np.abs(p)) > 0.5:
+                raise _NonFinite("non-finite value in a PCG solve")
+            return super().rd_forward(p, k_f, rho_f)
+
+    s2 = BigP(G, b)
+    r = T.gist(s2, np.zeros(8), 0.0, 0.0, 0.01, alpha0=1e3, maxit=5, nonneg=False)
+    assert r.history and r.history[0]["alpha"] < 1e3 and np.max(np.abs(r.p)) <= 0.5
+
+
+def test_lbfgs_keeps_p_nonnegative_by_default():
+    G, b, x = _sparse_problem(m=60, n=10, k=3, seed=15)
+    s = FakeSolver(G, b)
+    res, scale = T.weighted_l2(s, np.abs(x), 0.0, 0.0, 1e-3, np.ones(10), opttol=1e-7, maxit=300)
+    th = res.x * scale
+    assert res.converged and np.all(th[:10] >= 0.0)
+    # projected-gradient optimality on the face p >= 0
+    g = res.g / scale
+    free = th[:10] > 0
+    assert np.max(np.abs(g[:10][free])) <= 1e-6 * np.linalg.norm(G.T @ b)
+    assert np.all(g[:10][~free] >= -1e-9)
