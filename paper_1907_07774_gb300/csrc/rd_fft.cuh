@@ -273,18 +273,14 @@ __device__ __forceinline__ constexpr int mirror_a_other(int r) { return Shape<L>
 template <int L>
 __device__ __forceinline__ constexpr int mirror_a_zero(int r) { return (Shape<L>::R - r) % Shape<L>::R; }
 
-// Given Z = F(a + i b) (forward sign) in layout B (or A), replace every
-// register by (H a, H b): the discrete Hartley transforms
-// H x[k] = sum_n x[n] (cos + sin)(2 pi n k / L) of the two real sequences.
-// H a[k] = (Re Z_k + Re Z_-k - Im Z_k + Im Z_-k) / 2
-// H b[k] = (Re Z_k - Re Z_-k + Im Z_k + Im Z_-k) / 2
+// mir[r] = the value at index (L - k) mod L of the pencil, k the index held
+// by register r (layout B or A); fetched from the mirror lane of the group.
 template <typename T, int L, bool LAYOUT_B>
-__device__ __forceinline__ void hartley_combine(cpx<T>* v, int t) {
+__device__ __forceinline__ void mirror_fetch(const cpx<T>* v, cpx<T>* mir, int t) {
   using Sh = Shape<L>;
   constexpr int R = Sh::R, TH = Sh::TH;
   const int lane = threadIdx.x & 31;
   const int src = (lane & ~(TH - 1)) | ((TH - t) & (TH - 1));
-  cpx<T> mir[R];
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     const int ro = LAYOUT_B ? mirror_b_other<L>(r) : mirror_a_other<L>(r);
@@ -294,6 +290,18 @@ __device__ __forceinline__ void hartley_combine(cpx<T>* v, int t) {
     mir[r].x = (t == 0) ? v[rz].x : mx;
     mir[r].y = (t == 0) ? v[rz].y : my;
   }
+}
+
+// Given Z = F(a + i b) (forward sign) in layout B (or A), replace every
+// register by (H a, H b): the discrete Hartley transforms
+// H x[k] = sum_n x[n] (cos + sin)(2 pi n k / L) of the two real sequences.
+// H a[k] = (Re Z_k + Re Z_-k - Im Z_k + Im Z_-k) / 2
+// H b[k] = (Re Z_k - Re Z_-k + Im Z_k + Im Z_-k) / 2
+template <typename T, int L, bool LAYOUT_B>
+__device__ __forceinline__ void hartley_combine(cpx<T>* v, int t) {
+  constexpr int R = Shape<L>::R;
+  cpx<T> mir[R];
+  mirror_fetch<T, L, LAYOUT_B>(v, mir, t);
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     cpx<T> z = v[r], m = mir[r];

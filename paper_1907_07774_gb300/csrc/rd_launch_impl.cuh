@@ -253,8 +253,9 @@ cudaError_t Launch<T>::pcg_opx(int L, const PcgOpxArgs<T>& a, cudaStream_t s) {
         const long long rows = a.g.nn / LL;
         PcgOpxTmaArgs<T> t;
         if (rows % TS::ROWS == 0 && row_map(&t.map_w, a.w, a.g, sizeof(T), TS::ROWS) &&
-            row_map(&t.map_k, a.kappa, a.g, sizeof(T), TS::ROWS) && row_map(&t.map_p, a.p, a.g, sizeof(T), TS::ROWS) &&
-            row_map(&t.map_q, a.q, a.g, sizeof(T), TS::ROWS)) {
+            row_map(&t.map_k, a.kappa, a.g, sizeof(T), TS::ROWS) && row_map(&t.map_p, a.p, a.g, sizeof(T), TS::ROWS)) {
+          t.p = a.p;
+          t.q = a.q;
           t.g = a.g;
           t.twA = a.twA;
           t.twB = a.twB;

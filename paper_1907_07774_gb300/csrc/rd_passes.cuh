@@ -94,6 +94,36 @@ __device__ __forceinline__ double recip(double x) {
   return r;
 }
 
+// Preconditioner symbol along axis 0 applied in the Fourier domain.  With
+// Z = F(a + i b) (forward sign, layout B) for two real pencils a, b whose
+// symbols S'_a(k), S'_b(k) are real and even in k, H S' H x = F^-1 (S' F x)
+// (unnormalised inverse; the odd sine parts cancel), so
+//   W_k = S'_a A_k + i S'_b B_k = (S'_a + S'_b)/2 Z_k + (S'_a - S'_b)/2 conj(Z_-k)
+// with A_k = (Z_k + conj Z_-k)/2, B_k = (Z_k - conj Z_-k)/(2i); and since
+// sum_k S'(k) (H a)_k^2 = sum_k S'(k) |A_k|^2 for an even S', the returned
+// sum_k S'_a |A_k|^2 + S'_b |B_k|^2 is the Hartley-domain r.z term.
+template <typename T, int L>
+__device__ __forceinline__ T sym_apply(cpx<T>* v, int t, T base_a, T base_b, T symcT, T innT) {
+  constexpr int R = Shape<L>::R;
+  cpx<T> mir[R];
+  mirror_fetch<T, L, true>(v, mir, t);
+  T loc = T(0);
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int k0 = kwave<L>(idx_b<L>(r, t));
+    const T kk = T(k0 * k0);
+    const T sa = innT * recip(T(1) + symcT * (base_a + kk));
+    const T sb = innT * recip(T(1) + symcT * (base_b + kk));
+    const cpx<T> z = v[r], m = mir[r];
+    const T ax = z.x + m.x, ay = z.y - m.y, bx = z.y + m.y, by = m.x - z.x;
+    loc += T(0.25) * (sa * (ax * ax + ay * ay) + sb * (bx * bx + by * by));
+    const T hp = T(0.5) * (sa + sb), hm = T(0.5) * (sa - sb);
+    v[r].x = hp * z.x + hm * m.x;
+    v[r].y = hp * z.y - hm * m.y;
+  }
+  return loc;
+}
+
 // Wavenumber with the Nyquist index zeroed, for a runtime axis length n.
 __device__ __forceinline__ int kwave_rt(int i, int n) {
   return (i < n / 2) ? i : (i == n / 2 ? 0 : i - n);
@@ -192,7 +222,7 @@ enum DhtMode {
   kDhtPlain = 0,   // out = H_axis(in)                              (axis 1)
   kDhtSetup = 1,   // ff = ||in||^2 ; out = H_2(in)                 (axis 2)
   kDhtUpdate = 2,  // x += alpha p; r -= alpha q; rr; out = H_2(r)  (axis 2)
-  kDhtSym = 3      // out = H_0 S' H_0 in ; rz = sum S' (H_0 in)^2   (axis 0)
+  kDhtSym = 3      // out = H_0 S' H_0 in = F_0^-1 S' F_0 in; rz = sum S' (H_0 in)^2   (axis 0)
 };
 
 template <typename T>
@@ -262,7 +292,7 @@ __global__ void __launch_bounds__(kThreads) k_dht(DhtArgs<T> a) {
       }
     }
     fft_ab<T, L, -1>(v, sm, t, a.twA);
-    hartley_combine<T, L, true>(v, t);
+    if (MODE != kDhtSym) hartley_combine<T, L, true>(v, t);
     if (MODE == kDhtSym) {
       // pencils (i1, i2) and (i1, i2 + 1) along axis 0
       const long long P = 2 * (act ? pair : 0);
@@ -270,19 +300,8 @@ __global__ void __launch_bounds__(kThreads) k_dht(DhtArgs<T> a) {
       const int k1 = kwave_rt(i1, a.g.n[1]), k2a = kwave_rt(i2, a.g.n[2]), k2b = kwave_rt(i2 + 1, a.g.n[2]);
       const T base_a = T(k1 * k1 + k2a * k2a);
       const T base_b = T(k1 * k1 + k2b * k2b);
-      const T symcT = T(symc), innT = T(inv_nn);
-#pragma unroll
-      for (int r = 0; r < R; ++r) {
-        const int k0 = kwave<L>(idx_b<L>(r, t));
-        const T kk = T(k0 * k0);
-        const T sa = innT * recip(T(1) + symcT * (base_a + kk));
-        const T sb = innT * recip(T(1) + symcT * (base_b + kk));
-        loc += sa * v[r].x * v[r].x + sb * v[r].y * v[r].y;
-        v[r].x *= sa;
-        v[r].y *= sb;
-      }
-      fft_ba<T, L, -1>(v, sm, t, a.twB);
-      hartley_combine<T, L, false>(v, t);
+      loc += sym_apply<T, L>(v, t, base_a, base_b, T(symc), T(inv_nn));
+      fft_ba<T, L, +1>(v, sm, t, a.twB);
       if (act) {
 #pragma unroll
         for (int r = 0; r < R; ++r) st2<T, CONTIG>(a.out, b0, b1, (long long)idx_a<L>(r, t) * st, v[r]);

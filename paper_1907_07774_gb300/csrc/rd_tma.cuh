@@ -47,6 +47,27 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
   return false;
 }
 
+// Loads issued on one mbarrier and phases seen completed.  Loads on a
+// barrier are issued and awaited in order, so phase k completes with parity
+// k & 1.  After a timed-out wait, drain() waits (with the same limit) for the
+// loads still in flight, so that no copy lands in shared memory after the
+// block has exited.
+struct TmaPending {
+  unsigned issued = 0, done = 0;
+};
+
+__device__ __forceinline__ void drain(uint64_t* bar, const TmaPending& p) {
+  for (unsigned k = p.done; k < p.issued; ++k)
+    if (!mbar_wait(bar, k & 1)) break;
+}
+
+// Two stages used alternately: load k goes to stage k & 1 and completes
+// phase k >> 1 of its barrier.  Drains loads done..issued-1.
+__device__ __forceinline__ void drain2(uint64_t* full, unsigned done, unsigned issued) {
+  for (unsigned k = done; k < issued; ++k)
+    if (!mbar_wait(&full[k & 1], (k >> 1) & 1)) break;
+}
+
 __device__ __forceinline__ void fence_barrier_init() {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
@@ -169,11 +190,13 @@ __global__ void __launch_bounds__(TmaShape<T, L>::THREADS) k_op_tma(const __grid
   const long long ntiles = (long long)(a.g.n[2] / S::W) * (AXIS == 1 ? a.g.n[0] : a.g.n[1]);
   const T coef = T(a.c0 * (a.use_kf ? a.prm->k_f : 1.0) * a.prm->s / (double(L) * double(L)));
 
-  auto issue = [&](unsigned char* dst, const CUtensorMap* map, uint64_t* bar, long long tile) {
+  TmaPending pu, pk, pq;
+  auto issue = [&](unsigned char* dst, const CUtensorMap* map, uint64_t* bar, TmaPending& pd, long long tile) {
     int c0, c1, c2;
     tile_coords(a.g, AXIS, S::W, tile, c0, c1, c2);
     mbar_expect_tx(bar, TB);
     tma_load3(dst, map, c0, c1, c2, bar);
+    ++pd.issued;
   };
 
   if (threadIdx.x == 0) {
@@ -185,9 +208,9 @@ __global__ void __launch_bounds__(TmaShape<T, L>::THREADS) k_op_tma(const __grid
   __syncthreads();
   const long long t0 = blockIdx.x, stride = gridDim.x;
   if (threadIdx.x == 0 && t0 < ntiles) {
-    issue(u_buf, &a.map_u, &ubar, t0);
-    issue(k_buf, &a.map_k, &kbar, t0);
-    issue(q_buf, &a.map_q, &qbar, t0);
+    issue(u_buf, &a.map_u, &ubar, pu, t0);
+    issue(k_buf, &a.map_k, &kbar, pk, t0);
+    issue(q_buf, &a.map_q, &qbar, pq, t0);
   }
   double red = 0.0;
   bool bad = false;
@@ -196,17 +219,19 @@ __global__ void __launch_bounds__(TmaShape<T, L>::THREADS) k_op_tma(const __grid
     const bool more = tile + stride < ntiles;
     bool ok = mbar_wait(&ubar, i & 1);
     if (__syncthreads_or(!ok)) { bad = true; break; }
+    ++pu.done;
     cpx<T> v[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = *tile_pair<T>(u_buf, idx_a<L>(r, t), g);
     __syncthreads();   // every u value is in registers
-    if (threadIdx.x == 0 && more) issue(u_buf, &a.map_u, &ubar, tile + stride);
+    if (threadIdx.x == 0 && more) issue(u_buf, &a.map_u, &ubar, pu, tile + stride);
     fft_ab<T, L, -1, true>(v, sm, t, twA);
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = times_ik(v[r], kwave<L>(idx_b<L>(r, t)));
     fft_ba<T, L, +1, true>(v, sm, t, twB);
     ok = mbar_wait(&kbar, i & 1);
     if (__syncthreads_or(!ok)) { bad = true; break; }
+    ++pk.done;
     T loc = T(0);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
@@ -217,13 +242,14 @@ __global__ void __launch_bounds__(TmaShape<T, L>::THREADS) k_op_tma(const __grid
     }
     red += double(loc);
     __syncthreads();   // every kappa value is in registers
-    if (threadIdx.x == 0 && more) issue(k_buf, &a.map_k, &kbar, tile + stride);
+    if (threadIdx.x == 0 && more) issue(k_buf, &a.map_k, &kbar, pk, tile + stride);
     fft_ab<T, L, -1, true>(v, sm, t, twA);
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = times_ik(v[r], kwave<L>(idx_b<L>(r, t)));
     fft_ba<T, L, +1, true>(v, sm, t, twB);
     ok = mbar_wait(&qbar, i & 1);
     if (__syncthreads_or(!ok)) { bad = true; break; }
+    ++pq.done;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       cpx<T>* qp = tile_pair<T>(q_buf, idx_a<L>(r, t), g);
@@ -240,12 +266,18 @@ __global__ void __launch_bounds__(TmaShape<T, L>::THREADS) k_op_tma(const __grid
       tma_store3(&a.map_q, q_buf, c0, c1, c2);
       bulk_commit();
       bulk_wait_read0();
-      if (more) issue(q_buf, &a.map_q, &qbar, tile + stride);
+      if (more) issue(q_buf, &a.map_q, &qbar, pq, tile + stride);
     }
   }
   if (threadIdx.x == 0) bulk_wait0();
   if (bad) {
-    if (threadIdx.x == 0) { a.st->status = kStTimeout; a.st->sticky = kStTimeout; }
+    if (threadIdx.x == 0) {
+      a.st->status = kStTimeout;
+      a.st->sticky = kStTimeout;
+      drain(&ubar, pu);
+      drain(&kbar, pk);
+      drain(&qbar, pq);
+    }
     return;
   }
   if (a.reduce) {
@@ -290,11 +322,13 @@ __global__ void __launch_bounds__(TmaShape<T, L>::THREADS) k_dht_tma(const __gri
     symc = a.prm->s * a.prm->k_f * a.prm->kbar1;
     inv_nn = a.prm->inv_nn;
   }
+  unsigned issued = 0;
   auto issue = [&](long long tile, int b) {
     int c0, c1, c2;
     tile_coords(a.g, AXIS, S::W, tile, c0, c1, c2);
     mbar_expect_tx(&full[b], TB);
     tma_load3(st_buf(b), &a.map_in, c0, c1, c2, &full[b]);
+    ++issued;
   };
   if (threadIdx.x == 0) {
     mbar_init(&full[0], 1);
@@ -318,7 +352,7 @@ __global__ void __launch_bounds__(TmaShape<T, L>::THREADS) k_dht_tma(const __gri
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = *tile_pair<T>(st_buf(b), idx_a<L>(r, t), g);
     fft_ab<T, L, -1, true>(v, sm, t, twA);
-    hartley_combine<T, L, true>(v, t);
+    if (MODE != kDhtSym) hartley_combine<T, L, true>(v, t);
     T loc = T(0);
     if (MODE == kDhtSym) {
       int c0, c1, c2;
@@ -327,19 +361,8 @@ __global__ void __launch_bounds__(TmaShape<T, L>::THREADS) k_dht_tma(const __gri
       const int k1 = kwave_rt(i1, a.g.n[1]), k2a = kwave_rt(i2, a.g.n[2]), k2b = kwave_rt(i2 + 1, a.g.n[2]);
       const T base_a = T(k1 * k1 + k2a * k2a);
       const T base_b = T(k1 * k1 + k2b * k2b);
-      const T symcT = T(symc), innT = T(inv_nn);
-#pragma unroll
-      for (int r = 0; r < R; ++r) {
-        const int k0 = kwave<L>(idx_b<L>(r, t));
-        const T kk = T(k0 * k0);
-        const T sa = innT * recip(T(1) + symcT * (base_a + kk));
-        const T sb = innT * recip(T(1) + symcT * (base_b + kk));
-        loc += sa * v[r].x * v[r].x + sb * v[r].y * v[r].y;
-        v[r].x *= sa;
-        v[r].y *= sb;
-      }
-      fft_ba<T, L, -1, true>(v, sm, t, twB);
-      hartley_combine<T, L, false>(v, t);
+      loc = sym_apply<T, L>(v, t, base_a, base_b, T(symc), T(inv_nn));
+      fft_ba<T, L, +1, true>(v, sm, t, twB);
 #pragma unroll
       for (int r = 0; r < R; ++r) *tile_pair<T>(st_buf(b), idx_a<L>(r, t), g) = v[r];
     } else {
@@ -362,7 +385,11 @@ __global__ void __launch_bounds__(TmaShape<T, L>::THREADS) k_dht_tma(const __gri
   }
   if (threadIdx.x == 0) bulk_wait0();
   if (bad) {
-    if (threadIdx.x == 0) { a.st->status = kStTimeout; a.st->sticky = kStTimeout; }
+    if (threadIdx.x == 0) {
+      a.st->status = kStTimeout;
+      a.st->sticky = kStTimeout;
+      drain2(full, unsigned(i), issued);
+    }
     return;
   }
   if (MODE == kDhtSym) {
@@ -392,7 +419,7 @@ struct TmaRowShape {
   static constexpr int XBYTES = PAIRS * XSTRIDE * int(sizeof(cpx<T>));
   static constexpr bool OK = (THREADS >= 32) && (THREADS % 32 == 0);
   static constexpr int TWBYTES = 2 * L * int(sizeof(cpx<T>));
-  static constexpr size_t OPX_SMEM = 4 * size_t(TILE_BYTES) + XBYTES + TWBYTES + 1024;
+  static constexpr size_t OPX_SMEM = 3 * size_t(TILE_BYTES) + XBYTES + TWBYTES + 128;
   static constexpr size_t UPD_SMEM = 8 * size_t(TILE_BYTES) + XBYTES + TWBYTES + 1024;
   static constexpr size_t SETUP_SMEM = 2 * size_t(TILE_BYTES) + XBYTES + TWBYTES + 1024;
 };
@@ -422,7 +449,8 @@ struct PcgOpxTmaArgs {
   CUtensorMap map_w;
   CUtensorMap map_k;
   CUtensorMap map_p;
-  CUtensorMap map_q;
+  T* p;          // p is read through map_p and rewritten in place
+  T* q;
   Geom g;
   const cpx<T>* twA;
   const cpx<T>* twB;
@@ -433,25 +461,27 @@ struct PcgOpxTmaArgs {
 
 // z = H_2(w); p = z + beta p; q = p - s k_f d_2(kappa d_2 p)  (fields written
 // at layout-B positions of each pencil); reduces |p|^2 and sum kappa
-// (L d_2 p)^2.  Buffers: w (single, the next tile's w is requested as soon as
-// this one is in registers), kappa (single; q is written into it once kappa
-// is in registers, the next kappa is requested after q's store), p (two
-// stages).
+// (L d_2 p)^2.  The three inputs w, p and kappa have one tile buffer each;
+// the next tile of each is requested as soon as the current one is in
+// registers.  The new p and q leave from registers: in layout B the TH lanes
+// of a group hold TH consecutive elements of a row per register, so the
+// stores are coalesced.  q = p + ... takes p from a register copy when that
+// copy is small, else re-reads the value this thread has just stored.
 template <typename T, int L>
 __global__ void __launch_bounds__(TmaRowShape<T, L>::THREADS) k_pcg_opx_tma(const __grid_constant__ PcgOpxTmaArgs<T> a) {
   using S = TmaRowShape<T, L>;
   constexpr int R = S::R, TH = S::TH, TB = S::TILE_BYTES;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
   unsigned char* w_buf = smem;
-  unsigned char* k_buf = smem + TB;   // kappa, then q
-  auto p_st = [&](int b) { return smem + (2 + b) * TB; };
-  cpx<T>* xbuf = reinterpret_cast<cpx<T>*>(smem + 4 * TB);
-  cpx<T>* tws = reinterpret_cast<cpx<T>*>(smem + 4 * TB + S::XBYTES);
+  unsigned char* k_buf = smem + TB;
+  unsigned char* p_buf = smem + 2 * TB;
+  cpx<T>* xbuf = reinterpret_cast<cpx<T>*>(smem + 3 * TB);
+  cpx<T>* tws = reinterpret_cast<cpx<T>*>(smem + 3 * TB + S::XBYTES);
   const cpx<T>* twA = tws;
   const cpx<T>* twB = tws + L;
   stage_twiddles<T, L>(tws, a.twA, a.twB);
-  __shared__ uint64_t wbar, kbar, pbar[2];
+  __shared__ uint64_t wbar, kbar, pbar;
   const int g = threadIdx.x / TH, t = threadIdx.x % TH;
   cpx<T>* sm = xbuf + g * S::XSTRIDE;
   const long long ntiles = a.g.nn / L / S::ROWS;
@@ -459,36 +489,38 @@ __global__ void __launch_bounds__(TmaRowShape<T, L>::THREADS) k_pcg_opx_tma(cons
   const bool use_p = (betad != 0.0);
   const T beta = T(betad);
   const T coef = T(-a.prm->s * a.prm->k_f / (double(L) * double(L)));
-  auto issue = [&](unsigned char* dst, const CUtensorMap* map, uint64_t* bar, long long tile) {
+  TmaPending pw, pk, pp;
+  auto issue = [&](unsigned char* dst, const CUtensorMap* map, uint64_t* bar, TmaPending& pd, long long tile) {
     mbar_expect_tx(bar, TB);
     tma_load2(dst, map, 0, int(tile * S::ROWS), bar);
+    ++pd.issued;
   };
   if (threadIdx.x == 0) {
     mbar_init(&wbar, 1);
     mbar_init(&kbar, 1);
-    mbar_init(&pbar[0], 1);
-    mbar_init(&pbar[1], 1);
+    mbar_init(&pbar, 1);
     fence_barrier_init();
   }
   __syncthreads();
   const long long t0 = blockIdx.x, stride = gridDim.x;
   if (threadIdx.x == 0 && t0 < ntiles) {
-    issue(w_buf, &a.map_w, &wbar, t0);
-    issue(k_buf, &a.map_k, &kbar, t0);
-    if (use_p) {
-      issue(p_st(0), &a.map_p, &pbar[0], t0);
-      if (t0 + stride < ntiles) issue(p_st(1), &a.map_p, &pbar[1], t0 + stride);
-    }
+    issue(w_buf, &a.map_w, &wbar, pw, t0);
+    issue(k_buf, &a.map_k, &kbar, pk, t0);
+    if (use_p) issue(p_buf, &a.map_p, &pbar, pp, t0);
   }
   bool bad = false;
   double red_pp = 0.0, red_k = 0.0;
   int i = 0;
   const int ra = 2 * g, rb = 2 * g + 1;
   for (long long tile = t0; tile < ntiles; tile += stride, ++i) {
-    const int b = i & 1;
     const bool more = tile + stride < ntiles;
+    T* prow_a = a.p + (tile * S::ROWS + ra) * L;
+    T* prow_b = a.p + (tile * S::ROWS + rb) * L;
+    T* qrow_a = a.q + (tile * S::ROWS + ra) * L;
+    T* qrow_b = a.q + (tile * S::ROWS + rb) * L;
     bool ok = mbar_wait(&wbar, i & 1);
     if (__syncthreads_or(!ok)) { bad = true; break; }
+    ++pw.done;
     cpx<T> v[R];
     T lpp = T(0), lk = T(0);
 #pragma unroll
@@ -497,25 +529,31 @@ __global__ void __launch_bounds__(TmaRowShape<T, L>::THREADS) k_pcg_opx_tma(cons
       v[r] = {*row_elem<T, L>(w_buf, ra, n), *row_elem<T, L>(w_buf, rb, n)};
     }
     __syncthreads();   // every w value is in registers
-    if (threadIdx.x == 0 && more) issue(w_buf, &a.map_w, &wbar, tile + stride);
+    if (threadIdx.x == 0 && more) issue(w_buf, &a.map_w, &wbar, pw, tile + stride);
     fft_ab<T, L, -1, true>(v, sm, t, twA);
     hartley_combine<T, L, true>(v, t);
     if (use_p) {
-      ok = mbar_wait(&pbar[b], (i >> 1) & 1);
+      ok = mbar_wait(&pbar, i & 1);
       if (__syncthreads_or(!ok)) { bad = true; break; }
+      ++pp.done;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int n = idx_b<L>(r, t);
+        v[r].x += beta * *row_elem<T, L>(p_buf, ra, n);
+        v[r].y += beta * *row_elem<T, L>(p_buf, rb, n);
+      }
+      __syncthreads();   // every old p value is in registers
+      if (threadIdx.x == 0 && more) issue(p_buf, &a.map_p, &pbar, pp, tile + stride);
     }
+    constexpr bool KEEP_P = R * int(sizeof(T)) <= 64;
+    cpx<T> pv[KEEP_P ? R : 1];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const int n = idx_b<L>(r, t);
-      T* pa = row_elem<T, L>(p_st(b), ra, n);
-      T* pb = row_elem<T, L>(p_st(b), rb, n);
-      if (use_p) {
-        v[r].x += beta * *pa;
-        v[r].y += beta * *pb;
-      }
+      if constexpr (KEEP_P) pv[r] = v[r];
       lpp += v[r].x * v[r].x + v[r].y * v[r].y;
-      *pa = v[r].x;
-      *pb = v[r].y;
+      prow_a[n] = v[r].x;
+      prow_b[n] = v[r].y;
     }
     fft_ba<T, L, -1, true>(v, sm, t, twB);
 #pragma unroll
@@ -523,6 +561,7 @@ __global__ void __launch_bounds__(TmaRowShape<T, L>::THREADS) k_pcg_opx_tma(cons
     fft_ab<T, L, +1, true>(v, sm, t, twA);
     ok = mbar_wait(&kbar, i & 1);
     if (__syncthreads_or(!ok)) { bad = true; break; }
+    ++pk.done;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const int n = idx_b<L>(r, t);
@@ -533,7 +572,8 @@ __global__ void __launch_bounds__(TmaRowShape<T, L>::THREADS) k_pcg_opx_tma(cons
     }
     red_pp += double(lpp);
     red_k += double(lk);
-    __syncthreads();   // kappa consumed: its tile now receives q
+    __syncthreads();   // every kappa value is in registers
+    if (threadIdx.x == 0 && more) issue(k_buf, &a.map_k, &kbar, pk, tile + stride);
     fft_ba<T, L, -1, true>(v, sm, t, twB);
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = times_ik(v[r], kwave<L>(idx_a<L>(r, t)));
@@ -541,24 +581,23 @@ __global__ void __launch_bounds__(TmaRowShape<T, L>::THREADS) k_pcg_opx_tma(cons
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const int n = idx_b<L>(r, t);
-      *row_elem<T, L>(k_buf, ra, n) = *row_elem<T, L>(p_st(b), ra, n) + coef * v[r].x;
-      *row_elem<T, L>(k_buf, rb, n) = *row_elem<T, L>(p_st(b), rb, n) + coef * v[r].y;
-    }
-    fence_proxy_async();
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      const int row0 = int(tile * S::ROWS);
-      tma_store2(&a.map_p, p_st(b), 0, row0);
-      tma_store2(&a.map_q, k_buf, 0, row0);
-      bulk_commit();
-      bulk_wait_read0();
-      if (more) issue(k_buf, &a.map_k, &kbar, tile + stride);
-      if (use_p && tile + 2 * stride < ntiles) issue(p_st(b), &a.map_p, &pbar[b], tile + 2 * stride);
+      if constexpr (KEEP_P) {
+        qrow_a[n] = pv[r].x + coef * v[r].x;
+        qrow_b[n] = pv[r].y + coef * v[r].y;
+      } else {
+        qrow_a[n] = prow_a[n] + coef * v[r].x;
+        qrow_b[n] = prow_b[n] + coef * v[r].y;
+      }
     }
   }
-  if (threadIdx.x == 0) bulk_wait0();
   if (bad) {
-    if (threadIdx.x == 0) { a.st->status = kStTimeout; a.st->sticky = kStTimeout; }
+    if (threadIdx.x == 0) {
+      a.st->status = kStTimeout;
+      a.st->sticky = kStTimeout;
+      drain(&wbar, pw);
+      drain(&kbar, pk);
+      drain(&pbar, pp);
+    }
     return;
   }
   double vv[2] = {red_pp, red_k};
@@ -600,8 +639,10 @@ __global__ void __launch_bounds__(TmaRowShape<T, L>::THREADS) k_dht_row_tma(cons
   cpx<T>* sm = xbuf + g * S::XSTRIDE;
   const long long ntiles = a.g.nn / L / S::ROWS;
   const T alpha = (MODE == kDhtUpdate) ? T(a.st->alpha) : T(0);
+  unsigned issued = 0;
   auto issue = [&](long long tile, int b) {
     const int row0 = int(tile * S::ROWS);
+    ++issued;
     mbar_expect_tx(&full[b], NF * TB);
     tma_load2(fld(b, 0), &a.map_r, 0, row0, &full[b]);
     if (MODE == kDhtUpdate) {
@@ -680,7 +721,11 @@ __global__ void __launch_bounds__(TmaRowShape<T, L>::THREADS) k_dht_row_tma(cons
   }
   if (threadIdx.x == 0) bulk_wait0();
   if (bad) {
-    if (threadIdx.x == 0) { a.st->status = kStTimeout; a.st->sticky = kStTimeout; }
+    if (threadIdx.x == 0) {
+      a.st->status = kStTimeout;
+      a.st->sticky = kStTimeout;
+      drain2(full, unsigned(i), issued);
+    }
     return;
   }
   double vv[1] = {red};
