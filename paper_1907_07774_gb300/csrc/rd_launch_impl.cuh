@@ -140,8 +140,14 @@ cudaError_t Launch<T>::op(int L, const OpArgs<T>& a, cudaStream_t s) {
           t.st = a.fin.st;
           t.fin = a.fin;
           const long long tiles = (long long)(a.g.n[2] / TS::W) * (a.axis == 1 ? a.g.n[0] : a.g.n[1]);
-          if (a.axis == 1) return launch_tma(k_op_tma<T, LL, 1>, TS::OP_SMEM, TS::THREADS, tiles, t, s, kcOpStrided);
-          return launch_tma(k_op_tma<T, LL, 0>, TS::OP_SMEM, TS::THREADS, tiles, t, s, kcOpStrided);
+          if constexpr (sizeof(T) == 4) {
+            if (a.axis == 1)
+              return launch_tma(k_op_tma_red<T, LL, 1>, TS::OPR_SMEM, TS::THREADS, tiles, t, s, kcOpStrided);
+            return launch_tma(k_op_tma_red<T, LL, 0>, TS::OPR_SMEM, TS::THREADS, tiles, t, s, kcOpStrided);
+          } else {
+            if (a.axis == 1) return launch_tma(k_op_tma<T, LL, 1>, TS::OP_SMEM, TS::THREADS, tiles, t, s, kcOpStrided);
+            return launch_tma(k_op_tma<T, LL, 0>, TS::OP_SMEM, TS::THREADS, tiles, t, s, kcOpStrided);
+          }
         }
       }
       break;

@@ -91,6 +91,15 @@ __device__ __forceinline__ void tma_store3(const CUtensorMap* map, const void* s
                : "memory");
 }
 
+// Element-wise add of a shared-memory tile into global memory (the add is
+// performed by the memory system; f32 element type from the tensor map).
+__device__ __forceinline__ void tma_reduce_add3(const CUtensorMap* map, const void* src, int c0, int c1, int c2) {
+  asm volatile("cp.reduce.async.bulk.tensor.3d.global.shared::cta.add.tile.bulk_group [%0, {%2, %3, %4}], [%1];" ::"l"(
+                   reinterpret_cast<uint64_t>(map)),
+               "r"(smem_addr(src)), "r"(c0), "r"(c1), "r"(c2)
+               : "memory");
+}
+
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait0() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
@@ -118,6 +127,7 @@ struct TmaShape {
   static constexpr bool OK = THREADS >= 32;           // whole warps only
   static constexpr int TWBYTES = 2 * L * int(sizeof(cpx<T>));
   static constexpr size_t OP_SMEM = 3 * size_t(TILE_BYTES) + XBYTES + TWBYTES + 1024;
+  static constexpr size_t OPR_SMEM = 2 * size_t(TILE_BYTES) + XBYTES + TWBYTES + 1024;
   static constexpr size_t DHT_SMEM = 2 * size_t(TILE_BYTES) + XBYTES + TWBYTES + 1024;
 };
 
@@ -224,7 +234,14 @@ __global__ void __launch_bounds__(TmaShape<T, L>::THREADS) k_op_tma(const __grid
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = *tile_pair<T>(u_buf, idx_a<L>(r, t), g);
     __syncthreads();   // every u value is in registers
-    if (threadIdx.x == 0 && more) issue(u_buf, &a.map_u, &ubar, pu, tile + stride);
+    if (threadIdx.x == 0) {
+      if (more) issue(u_buf, &a.map_u, &ubar, pu, tile + stride);
+      if (i > 0) {
+        // q_buf is free once the previous tile's store has read it
+        bulk_wait_read0();
+        issue(q_buf, &a.map_q, &qbar, pq, tile);
+      }
+    }
     fft_ab<T, L, -1, true>(v, sm, t, twA);
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = times_ik(v[r], kwave<L>(idx_b<L>(r, t)));
@@ -265,8 +282,6 @@ __global__ void __launch_bounds__(TmaShape<T, L>::THREADS) k_op_tma(const __grid
       tile_coords(a.g, AXIS, S::W, tile, c0, c1, c2);
       tma_store3(&a.map_q, q_buf, c0, c1, c2);
       bulk_commit();
-      bulk_wait_read0();
-      if (more) issue(q_buf, &a.map_q, &qbar, pq, tile + stride);
     }
   }
   if (threadIdx.x == 0) bulk_wait0();
@@ -277,6 +292,112 @@ __global__ void __launch_bounds__(TmaShape<T, L>::THREADS) k_op_tma(const __grid
       drain(&ubar, pu);
       drain(&kbar, pk);
       drain(&qbar, pq);
+    }
+    return;
+  }
+  if (a.reduce) {
+    double vv[1] = {red};
+    reduce_finish<1>(vv, a.fin);
+  }
+}
+
+// The same operator pass with the accumulation done by a TMA reduce-add
+// into q (FP32 fields): q is never loaded into the block, and the kappa
+// tile, once its values are in registers, stages coef * d(kappa d u) for
+// the reduction.  Two tiles plus the exchange area per block.  Each element
+// of q receives exactly one add per pass, so the result is deterministic.
+template <typename T, int L, int AXIS>
+__global__ void __launch_bounds__(TmaShape<T, L>::THREADS) k_op_tma_red(const __grid_constant__ OpTmaArgs<T> a) {
+  static_assert(sizeof(T) == 4, "the tensor reduce-add is used for FP32 fields");
+  using S = TmaShape<T, L>;
+  constexpr int R = S::R, TH = S::TH, TB = S::TILE_BYTES;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  unsigned char* u_buf = smem;
+  unsigned char* k_buf = smem + TB;   // kappa, then the tile added into q
+  cpx<T>* xbuf = reinterpret_cast<cpx<T>*>(smem + 2 * TB);
+  cpx<T>* tws = reinterpret_cast<cpx<T>*>(smem + 2 * TB + S::XBYTES);
+  const cpx<T>* twA = tws;
+  const cpx<T>* twB = tws + L;
+  stage_twiddles<T, L>(tws, a.twA, a.twB);
+  __shared__ uint64_t ubar, kbar;
+  const int g = threadIdx.x / TH, t = threadIdx.x % TH;
+  cpx<T>* sm = xbuf + g * S::XSTRIDE;
+  const long long ntiles = (long long)(a.g.n[2] / S::W) * (AXIS == 1 ? a.g.n[0] : a.g.n[1]);
+  const T coef = T(a.c0 * (a.use_kf ? a.prm->k_f : 1.0) * a.prm->s / (double(L) * double(L)));
+  TmaPending pu, pk;
+  auto issue = [&](unsigned char* dst, const CUtensorMap* map, uint64_t* bar, TmaPending& pd, long long tile) {
+    int c0, c1, c2;
+    tile_coords(a.g, AXIS, S::W, tile, c0, c1, c2);
+    mbar_expect_tx(bar, TB);
+    tma_load3(dst, map, c0, c1, c2, bar);
+    ++pd.issued;
+  };
+  if (threadIdx.x == 0) {
+    mbar_init(&ubar, 1);
+    mbar_init(&kbar, 1);
+    fence_barrier_init();
+  }
+  __syncthreads();
+  const long long t0 = blockIdx.x, stride = gridDim.x;
+  if (threadIdx.x == 0 && t0 < ntiles) {
+    issue(u_buf, &a.map_u, &ubar, pu, t0);
+    issue(k_buf, &a.map_k, &kbar, pk, t0);
+  }
+  double red = 0.0;
+  bool bad = false;
+  int i = 0;
+  for (long long tile = t0; tile < ntiles; tile += stride, ++i) {
+    const bool more = tile + stride < ntiles;
+    bool ok = mbar_wait(&ubar, i & 1);
+    if (__syncthreads_or(!ok)) { bad = true; break; }
+    ++pu.done;
+    cpx<T> v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = *tile_pair<T>(u_buf, idx_a<L>(r, t), g);
+    __syncthreads();   // every u value is in registers
+    if (threadIdx.x == 0 && more) issue(u_buf, &a.map_u, &ubar, pu, tile + stride);
+    fft_ab<T, L, -1, true>(v, sm, t, twA);
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = times_ik(v[r], kwave<L>(idx_b<L>(r, t)));
+    fft_ba<T, L, +1, true>(v, sm, t, twB);
+    ok = mbar_wait(&kbar, i & 1);
+    if (__syncthreads_or(!ok)) { bad = true; break; }
+    ++pk.done;
+    T loc = T(0);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      cpx<T> k = *tile_pair<T>(k_buf, idx_a<L>(r, t), g);
+      if (a.reduce) loc += k.x * v[r].x * v[r].x + k.y * v[r].y * v[r].y;
+      v[r].x *= k.x;
+      v[r].y *= k.y;
+    }
+    red += double(loc);
+    __syncthreads();   // every kappa value is in registers: k_buf is free
+    fft_ab<T, L, -1, true>(v, sm, t, twA);
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = times_ik(v[r], kwave<L>(idx_b<L>(r, t)));
+    fft_ba<T, L, +1, true>(v, sm, t, twB);
+#pragma unroll
+    for (int r = 0; r < R; ++r) *tile_pair<T>(k_buf, idx_a<L>(r, t), g) = {coef * v[r].x, coef * v[r].y};
+    fence_proxy_async();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int c0, c1, c2;
+      tile_coords(a.g, AXIS, S::W, tile, c0, c1, c2);
+      tma_reduce_add3(&a.map_q, k_buf, c0, c1, c2);
+      bulk_commit();
+      bulk_wait_read0();
+      if (more) issue(k_buf, &a.map_k, &kbar, pk, tile + stride);
+    }
+  }
+  if (threadIdx.x == 0) bulk_wait0();
+  if (bad) {
+    if (threadIdx.x == 0) {
+      a.st->status = kStTimeout;
+      a.st->sticky = kStTimeout;
+      drain(&ubar, pu);
+      drain(&kbar, pk);
     }
     return;
   }
@@ -351,6 +472,11 @@ __global__ void __launch_bounds__(TmaShape<T, L>::THREADS) k_dht_tma(const __gri
     cpx<T> v[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = *tile_pair<T>(st_buf(b), idx_a<L>(r, t), g);
+    if (threadIdx.x == 0 && i > 0 && tile + stride < ntiles) {
+      // the other stage is free once the previous tile's store has read it
+      bulk_wait_read0();
+      issue(tile + stride, b ^ 1);
+    }
     fft_ab<T, L, -1, true>(v, sm, t, twA);
     if (MODE != kDhtSym) hartley_combine<T, L, true>(v, t);
     T loc = T(0);
@@ -379,8 +505,6 @@ __global__ void __launch_bounds__(TmaShape<T, L>::THREADS) k_dht_tma(const __gri
       tile_coords(a.g, AXIS, S::W, tile, c0, c1, c2);
       tma_store3(&a.map_out, st_buf(b), c0, c1, c2);
       bulk_commit();
-      bulk_wait_read0();
-      if (tile + 2 * stride < ntiles) issue(tile + 2 * stride, b);
     }
   }
   if (threadIdx.x == 0) bulk_wait0();
@@ -694,6 +818,11 @@ __global__ void __launch_bounds__(TmaRowShape<T, L>::THREADS) k_dht_row_tma(cons
       v[r] = rv;
     }
     red += double(loc);
+    if (threadIdx.x == 0 && i > 0 && tile + stride < ntiles) {
+      // the other stage is free once the previous tile's stores have read it
+      bulk_wait_read0();
+      issue(tile + stride, b ^ 1);
+    }
     fft_ab<T, L, -1, true>(v, sm, t, twA);
     hartley_combine<T, L, true>(v, t);
     // Hartley values go to the p tile (update) or back into the r tile (setup)
@@ -715,8 +844,6 @@ __global__ void __launch_bounds__(TmaRowShape<T, L>::THREADS) k_dht_row_tma(cons
       }
       tma_store2(&a.map_out, ob, 0, row0);
       bulk_commit();
-      bulk_wait_read0();
-      if (tile + 2 * stride < ntiles) issue(tile + 2 * stride, b);
     }
   }
   if (threadIdx.x == 0) bulk_wait0();
