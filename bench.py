@@ -491,6 +491,82 @@ def run_gn(args, rank, world, local):
     return 0
 
 
+def run_picard(args, rank, world, local):
+    """The tumor side of one Picard step at 256^3, nt = 32 (mixed): the
+    Moving-Atlas gradient (D_c + D_m, anatomy final condition) with the
+    coupling field q(x) accumulated during the adjoint and read back to the
+    device, timed next to the plain gradient on the same problem."""
+    import numpy as np
+    torch = _gpu_setup(local)
+    from paper_1907_07774_gb300 import rd as R
+    from paper_1907_07774_gb300 import synth
+    prob = problem(args.n, args.nt)
+    plain, d = _calibrated_context(R, synth, torch, prob, "mixed", pcg_rtol=1e-6, pcg_maxit=500)
+    ma = R.context_for(prob, prec="mixed", pcg_rtol=1e-6, pcg_maxit=500, moving_atlas=True, coupling=True)
+    ma.rd_set_data(torch.from_numpy(d).cuda())
+    rng = np.random.default_rng(prob.seed + 11)
+    md = [np.clip(m + 0.05 * rng.standard_normal(prob.n), 0, 1) * (m > 0)
+          for m in (prob.m_wm, prob.m_gm, prob.m_csf)]
+    ma.rd_set_anatomy_data(*[torch.from_numpy(x).cuda() for x in md])
+    q = [torch.empty(prob.n, dtype=torch.float64, device="cuda") for _ in range(3)]
+    th = (prob.p, prob.k_f, prob.rho_f)
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            fn()
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t0) / args.steps
+
+    def ma_step():
+        ma.rd_gradient(*th)
+        ma.rd_coupling_field(*q)
+
+    t_ma = timed(ma_step)
+    t_plain = timed(lambda: plain.rd_gradient(*th))
+    cells = args.n ** 3 * args.nt
+    J, g = ma.rd_gradient(*th)
+    line = {"metric": "Moving-Atlas gradient + coupling field cell-updates/s at 256^3", "value": cells / t_ma,
+            "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_ma,
+            "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{args.n}^3 nt={args.nt} np=125 mixed, D_c + D_m objective, q(x) to device"},
+            "plain_gradient_ms": 1e3 * t_plain, "overhead_vs_plain": t_ma / t_plain - 1.0,
+            "misfit": J, "q_abs_max": [float(x.abs().max()) for x in q]}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_tumor_inv(args, rank, world, local):
+    """The paper's tumor optimiser (l1 GIST with the Hoyer beta search, then
+    weighted-l2 L-BFGS on (p, k_f)) at 128^3, nt = 16, 4^3 Gaussians, mixed;
+    reports wall time and solver counts."""
+    import numpy as np
+    torch = _gpu_setup(local)
+    from paper_1907_07774_gb300 import rd as R
+    from paper_1907_07774_gb300 import synth
+    from paper_1907_07774_gb300 import tumor_inv as T
+    prob = synth.calibration_problem(n=128, nt=16, m=4, sigma=2 * np.pi / 32)
+    ctx, _ = _calibrated_context(R, synth, torch, prob, "mixed", pcg_rtol=1e-6, pcg_maxit=500)
+    t0 = time.perf_counter()
+    out = T.tumor_inversion(ctx, rho_f=prob.rho_f_true, k_f_l2=0.02, beta_steps=5,
+                            gist_kw={"maxit": 30, "tau_j": 1e-5}, beta_l2=1e-4, opttol=1e-3, l2_maxit=25)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    evals = sum(t["iters"] for t in out.l1.tried)
+    line = {"metric": "tumor inversion (l1 GIST + Hoyer beta search, weighted-l2 L-BFGS) wall time at 128^3 (s)",
+            "value": dt, "unit": "s", "higher_is_better": False, "n_gpus": 1, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "128^3 nt=16 np=64 mixed, 5 beta bisection steps (GIST <= 30 iterations), "
+                                   "L-BFGS <= 25 iterations on (p, k_f)"},
+            "gist_iterations": evals, "lbfgs_iterations": out.l2.iters, "lbfgs_evaluations": out.l2.evals,
+            "beta_l1": out.beta_l1, "sparsity": out.sparsity, "nnz_l1": int(np.count_nonzero(out.l1.p)),
+            "misfit_final": out.misfit, "k_f_final": out.k_f}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -502,9 +578,11 @@ def main():
     ap.add_argument("--ckpt-stride", type=int, default=0)
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="gradient", choices=["gradient", "batch", "newton", "gn"],
+    ap.add_argument("--workload", default="gradient",
+                    choices=["gradient", "batch", "newton", "gn", "picard", "tumor_inv"],
                     help="gradient: the headline 256^3 gradient; batch: 48 uneven instances in one graph; "
-                         "newton: gradient + 20 Hessian-vector products; gn: Gauss-Newton calibration")
+                         "newton: gradient + 20 Hessian-vector products; gn: Gauss-Newton calibration; "
+                         "picard: Moving-Atlas gradient + coupling field; tumor_inv: l1/l2 tumor optimiser")
     ap.add_argument("--gn-iters", type=int, default=10)
     ap.add_argument("--autotune", action="store_true", help="tune grid sizes per kernel class first")
     args = ap.parse_args()
@@ -517,6 +595,10 @@ def main():
         return run_newton(args, rank, world, local)
     if args.workload == "gn":
         return run_gn(args, rank, world, local)
+    if args.workload == "picard":
+        return run_picard(args, rank, world, local)
+    if args.workload == "tumor_inv":
+        return run_tumor_inv(args, rank, world, local)
     return run_ours(args, rank, world, local)
 
 
