@@ -189,3 +189,110 @@ def random_directions(count, dim, seed):
     rng = np.random.default_rng(seed)
     v = rng.standard_normal((count, dim))
     return v / np.linalg.norm(v, axis=1, keepdims=True)
+
+
+# ------------------------------------------------------------ registration
+# Inputs of the registration sub-problem (atlas and patient anatomy, a fixed
+# tumor c(1), a coupling field q, divergence-free velocities).  Every field
+# is a trigonometric sum evaluated exactly at arbitrary points, so the
+# patient anatomy can be the atlas seen through a smooth displacement.
+@dataclass
+class TrigSum:
+    """``sum_w a_w cos(w.x) + b_w sin(w.x)`` with its analytic derivatives."""
+    modes: np.ndarray       # (M, 3) integer wave vectors
+    a: np.ndarray           # (M,)
+    b: np.ndarray           # (M,)
+
+    @staticmethod
+    def random(rng, radius, amp=1.0):
+        modes = half_space_modes(radius)
+        ab = rng.standard_normal((len(modes), 2)) * (amp / math.sqrt(len(modes)))
+        return TrigSum(modes, ab[:, 0].copy(), ab[:, 1].copy())
+
+    def _phase(self, X):
+        return sum(self.modes[:, a][:, None] * X[a].reshape(1, -1) for a in range(3))
+
+    def __call__(self, X):
+        shape = X[0].shape
+        out = np.zeros(X[0].size)
+        for lo in range(0, len(self.modes), 64):      # chunks keep memory small
+            sl = slice(lo, lo + 64)
+            ph = sum(self.modes[sl, a][:, None] * X[a].reshape(1, -1) for a in range(3))
+            out += self.a[sl] @ np.cos(ph) + self.b[sl] @ np.sin(ph)
+        return out.reshape(shape)
+
+    def deriv(self, X, axis):
+        shape = X[0].shape
+        out = np.zeros(X[0].size)
+        w = self.modes[:, axis].astype(np.float64)
+        for lo in range(0, len(self.modes), 64):
+            sl = slice(lo, lo + 64)
+            ph = sum(self.modes[sl, a][:, None] * X[a].reshape(1, -1) for a in range(3))
+            out += (w[sl] * self.b[sl]) @ np.cos(ph) - (w[sl] * self.a[sl]) @ np.sin(ph)
+        return out.reshape(shape)
+
+
+def coords_mesh(n):
+    x = grid_coords(n)
+    return np.meshgrid(x[0], x[1], x[2], indexing="ij")
+
+
+def curl_field(pots, X):
+    """``curl A`` of three trigonometric potentials at the points X:
+    divergence-free by construction."""
+    d = lambda c, a: pots[c].deriv(X, a)
+    return [d(2, 1) - d(1, 2), d(0, 2) - d(2, 0), d(1, 0) - d(0, 1)]
+
+
+def smooth_anatomy(fields, X, half_axes=HALF_AXES, width=0.15):
+    """Softmax of three smooth fields times a smooth ellipsoid indicator
+    ``1 / (1 + exp((r - 1) / width))``, r the ellipsoid radius."""
+    f = np.stack([fl(X) for fl in fields])
+    f -= f.max(axis=0, keepdims=True)
+    e = np.exp(f)
+    sm = e / e.sum(axis=0, keepdims=True)
+    r = np.sqrt(sum(((X[a] - math.pi) / half_axes[a]) ** 2 for a in range(3)))
+    mask = 1.0 / (1.0 + np.exp((r - 1.0) / width))
+    return [sm[i] * mask for i in range(3)]
+
+
+@dataclass
+class RegistrationProblem:
+    n: tuple
+    nt: int
+    m_atlas: list
+    m_patient: list
+    c1: np.ndarray
+    q: list
+    v: list            # a divergence-free test velocity
+    directions: list   # divergence-free directions (lists of 3 fields)
+    beta_v: float
+    seed: int
+
+
+def registration_problem(n=64, nt=8, seed=4000, radius=3, disp_amp=0.25, v_amp=0.3, q_amp=0.02,
+                         beta_v=1e-2, ndir=2):
+    """Atlas = smooth anatomy; patient = the atlas at ``x - u(x)`` with ``u``
+    a smooth divergence-free displacement of amplitude ``disp_amp``; tumor
+    c(1) = a Gaussian of width 0.5 at (pi, pi, pi) scaled to 0.9; q = small
+    smooth fields; a test velocity and directions as curls of random
+    potentials (wave vectors of norm <= radius)."""
+    n3 = (n, n, n) if np.isscalar(n) else tuple(int(k) for k in n)
+    rng = np.random.default_rng(seed)
+    X = coords_mesh(n3)
+    fields = [TrigSum.random(rng, radius, amp=2.0) for _ in range(3)]
+    m_atlas = smooth_anatomy(fields, X)
+    upot = [TrigSum.random(rng, 2, amp=disp_amp / 2.0) for _ in range(3)]
+    u = curl_field(upot, X)
+    m_patient = smooth_anatomy(fields, [X[a] - u[a] for a in range(3)])
+    r2 = sum((X[a] - math.pi) ** 2 for a in range(3))
+    c1 = 0.9 * np.exp(-r2 / (2 * 0.5 ** 2))
+    q = [TrigSum.random(rng, radius, amp=q_amp)(X) for _ in range(3)]
+    vpot = [TrigSum.random(rng, radius, amp=v_amp / radius) for _ in range(3)]
+    v = curl_field(vpot, X)
+    dirs = []
+    for _ in range(ndir):
+        pots = [TrigSum.random(rng, radius, amp=1.0 / radius) for _ in range(3)]
+        dirs.append(curl_field(pots, X))
+    return RegistrationProblem(n=n3, nt=nt, m_atlas=m_atlas, m_patient=m_patient, c1=c1, q=q, v=v,
+                               directions=dirs, beta_v=beta_v, seed=seed)
