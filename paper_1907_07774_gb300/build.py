@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "librd.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
-SOURCES = ["rd_kern_f32.cu", "rd_kern_f64.cu", "rd_api.cu", "rd_noalloc.cu"]
+SOURCES = ["rd_kern_f32.cu", "rd_kern_f64.cu", "rd_api.cu", "rd_noalloc.cu", "rd_reg.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE]
 
@@ -29,7 +29,7 @@ def _nvcc():
 
 def _inputs():
     files = [os.path.join(CSRC, f) for f in os.listdir(CSRC)]
-    files.append(os.path.join(INCLUDE, "rd.h"))
+    files += [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE)]
     return files
 
 

@@ -23,6 +23,7 @@
 
 #include "../../include/rd.h"
 #include "rd_launch.cuh"
+#include "rd_tables.h"
 
 namespace rd {
 
@@ -172,15 +173,7 @@ void prof_end(int token, cudaStream_t s) {
 
 namespace {
 
-constexpr double kTwoPi = 6.283185307179586476925286766559;
-constexpr int kNumL = 7;   // 8, 16, 32, 64, 128, 256 and 96
-inline int lidx(int L) {
-  if (L == 96) return 6;
-  int i = 0;
-  while ((8 << i) < L) ++i;
-  return i;
-}
-inline int slot_length(int i) { return i == 6 ? 96 : (8 << i); }
+constexpr double kTwoPi = kTwoPiHost;
 
 // Bump allocator over the caller's workspace (256-byte alignment).
 struct Carve {
@@ -195,14 +188,6 @@ struct Carve {
   }
 };
 
-inline bool is_device_ptr(const void* p) {
-  cudaPointerAttributes at;
-  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
-}
 
 enum Field {
   F_KAPPA1, F_RHO1, F_C0, F_D, F_ALPHA, F_AB, F_WS, F_CN, F_CS,
@@ -391,22 +376,7 @@ struct Engine : EngineBase {
     std::vector<cpx<T>> ta, tb;
     for (int i = 0; i < kNumL; ++i) {
       const int L = slot_length(i);
-      const int R = shape_r(L);
-      const int TH = L / R;
-      ta.assign(L, cpx<T>{T(0), T(0)});
-      tb.assign(L, cpx<T>{T(0), T(0)});
-      for (int k1 = 0; k1 < R; ++k1)
-        for (int t = 0; t < TH; ++t) {
-          const double th = kTwoPi * double((long long)t * k1 % L) / L;
-          ta[k1 * TH + t] = {T(std::cos(th)), T(-std::sin(th))};
-        }
-      for (int m = 0; m < R / TH; ++m)
-        for (int n2 = 0; n2 < TH; ++n2)
-          for (int j = 0; j < TH; ++j) {
-            const int k1 = j + TH * m;
-            const double th = kTwoPi * double((long long)n2 * k1 % L) / L;
-            tb[(m * TH + n2) * TH + j] = {T(std::cos(th)), T(std::sin(th))};
-          }
+      build_twiddles<T>(L, ta, tb);
       if ((e = cudaMemcpyAsync(twA[i], ta.data(), sizeof(cpx<T>) * L, cudaMemcpyHostToDevice, stream)) != cudaSuccess)
         return cuda_fail(e, "upload twiddles");
       if ((e = cudaMemcpyAsync(twB[i], tb.data(), sizeof(cpx<T>) * L, cudaMemcpyHostToDevice, stream)) != cudaSuccess)

@@ -23,6 +23,7 @@
 
 #include "../../include/rd.h"
 #include "rd_launch.cuh"
+#include "rd_tables.h"
 
 namespace rd {
 namespace {
@@ -56,13 +57,7 @@ struct DeviceSlot {
 std::mutex g_mu;
 DeviceSlot g_slots[kMaxDevices];
 
-int length_index(int L) {
-  if (L == 96) return 6;
-  int i = 0;
-  while ((8 << i) < L) ++i;
-  return i;
-}
-int slot_length(int i) { return i == 6 ? 96 : (8 << i); }
+int length_index(int L) { return lidx(L); }
 
 // Once per device, with that device current: find the array's device
 // address (the host-side symbol is only a stand-in) and upload the twiddle
@@ -80,25 +75,12 @@ rd_status setup_device(int dev, StaticScratch** out) {
     return RD_ERR_CUDA;
   }
   StaticScratch* d = reinterpret_cast<StaticScratch*>(p);
-  const double two_pi = 6.283185307179586476925286766559;
-  std::vector<cpx<double>> ta(kMaxLength), tb(kMaxLength);
+  std::vector<cpx<double>> ta, tb;
   for (int i = 0; i < kNumLengths; ++i) {
     const int L = slot_length(i);
-    const int R = shape_r(L);
-    const int TH = L / R;
-    for (auto& v : ta) v = {0.0, 0.0};
-    for (auto& v : tb) v = {0.0, 0.0};
-    for (int k1 = 0; k1 < R; ++k1)
-      for (int t = 0; t < TH; ++t) {
-        const double th = two_pi * double((long long)t * k1 % L) / L;
-        ta[k1 * TH + t] = {std::cos(th), -std::sin(th)};
-      }
-    for (int m = 0; m < R / TH; ++m)
-      for (int n2 = 0; n2 < TH; ++n2)
-        for (int j = 0; j < TH; ++j) {
-          const double th = two_pi * double((long long)n2 * (j + TH * m) % L) / L;
-          tb[(m * TH + n2) * TH + j] = {std::cos(th), std::sin(th)};
-        }
+    build_twiddles<double>(L, ta, tb);
+    ta.resize(kMaxLength, cpx<double>{0.0, 0.0});
+    tb.resize(kMaxLength, cpx<double>{0.0, 0.0});
     if (cudaMemcpy(&d->twA[i][0], ta.data(), sizeof(cpx<double>) * kMaxLength, cudaMemcpyHostToDevice) !=
             cudaSuccess ||
         cudaMemcpy(&d->twB[i][0], tb.data(), sizeof(cpx<double>) * kMaxLength, cudaMemcpyHostToDevice) !=

@@ -221,6 +221,21 @@ class TrigSum:
             out += self.a[sl] @ np.cos(ph) + self.b[sl] @ np.sin(ph)
         return out.reshape(shape)
 
+    def _grid_spectrum(self, n, coef):
+        spec = np.zeros(tuple(n), dtype=np.complex128)
+        idx = tuple((self.modes[:, a] % n[a]) for a in range(3))
+        np.add.at(spec, idx, coef)
+        return np.real(np.fft.ifftn(spec)) * float(np.prod(n))
+
+    def grid(self, n):
+        """The sum on the grid of ``n`` (same values as ``self(coords_mesh(n))``,
+        evaluated through one inverse DFT; exact while every |w_a| < n_a / 2)."""
+        return self._grid_spectrum(n, self.a - 1j * self.b)
+
+    def grid_deriv(self, n, axis):
+        """``d/dx_axis`` of the sum on the grid, exactly as :meth:`deriv`."""
+        return self._grid_spectrum(n, self.modes[:, axis] * (self.b + 1j * self.a))
+
     def deriv(self, X, axis):
         shape = X[0].shape
         out = np.zeros(X[0].size)
@@ -244,10 +259,17 @@ def curl_field(pots, X):
     return [d(2, 1) - d(1, 2), d(0, 2) - d(2, 0), d(1, 0) - d(0, 1)]
 
 
-def smooth_anatomy(fields, X, half_axes=HALF_AXES, width=0.15):
+def curl_field_grid(pots, n):
+    """:func:`curl_field` on the grid of ``n``."""
+    d = lambda c, a: pots[c].grid_deriv(n, a)
+    return [d(2, 1) - d(1, 2), d(0, 2) - d(2, 0), d(1, 0) - d(0, 1)]
+
+
+def smooth_anatomy(fields, X, half_axes=HALF_AXES, width=0.15, values=None):
     """Softmax of three smooth fields times a smooth ellipsoid indicator
-    ``1 / (1 + exp((r - 1) / width))``, r the ellipsoid radius."""
-    f = np.stack([fl(X) for fl in fields])
+    ``1 / (1 + exp((r - 1) / width))``, r the ellipsoid radius (``values``:
+    the three fields already evaluated at X)."""
+    f = np.stack(values if values is not None else [fl(X) for fl in fields])
     f -= f.max(axis=0, keepdims=True)
     e = np.exp(f)
     sm = e / e.sum(axis=0, keepdims=True)
@@ -281,18 +303,18 @@ def registration_problem(n=64, nt=8, seed=4000, radius=3, disp_amp=0.25, v_amp=0
     rng = np.random.default_rng(seed)
     X = coords_mesh(n3)
     fields = [TrigSum.random(rng, radius, amp=2.0) for _ in range(3)]
-    m_atlas = smooth_anatomy(fields, X)
+    m_atlas = smooth_anatomy(fields, X, values=[fl.grid(n3) for fl in fields])
     upot = [TrigSum.random(rng, 2, amp=disp_amp / 2.0) for _ in range(3)]
-    u = curl_field(upot, X)
+    u = curl_field_grid(upot, n3)
     m_patient = smooth_anatomy(fields, [X[a] - u[a] for a in range(3)])
     r2 = sum((X[a] - math.pi) ** 2 for a in range(3))
     c1 = 0.9 * np.exp(-r2 / (2 * 0.5 ** 2))
-    q = [TrigSum.random(rng, radius, amp=q_amp)(X) for _ in range(3)]
+    q = [TrigSum.random(rng, radius, amp=q_amp).grid(n3) for _ in range(3)]
     vpot = [TrigSum.random(rng, radius, amp=v_amp / radius) for _ in range(3)]
-    v = curl_field(vpot, X)
+    v = curl_field_grid(vpot, n3)
     dirs = []
     for _ in range(ndir):
         pots = [TrigSum.random(rng, radius, amp=1.0 / radius) for _ in range(3)]
-        dirs.append(curl_field(pots, X))
+        dirs.append(curl_field_grid(pots, n3))
     return RegistrationProblem(n=n3, nt=nt, m_atlas=m_atlas, m_patient=m_patient, c1=c1, q=q, v=v,
                                directions=dirs, beta_v=beta_v, seed=seed)

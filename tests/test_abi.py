@@ -1,4 +1,4 @@
-"""The C-ABI library loads and exports every symbol include/rd.h declares;
+"""The C-ABI library loads and exports every symbol include/*.h declares;
 host-only entry points validate their arguments (CPU only)."""
 
 import ctypes
@@ -20,13 +20,19 @@ def lib():
 
 
 def declared():
-    src = open(os.path.join(ROOT, "include", "rd.h")).read()
-    return sorted(set(re.findall(r"\b(rd_[a-z_]+)\s*\(", src)))
+    names = set()
+    inc = os.path.join(ROOT, "include")
+    for f in sorted(os.listdir(inc)):
+        if f.endswith(".h"):
+            src = open(os.path.join(inc, f)).read()
+            names |= set(re.findall(r"\b(r[dg]_[a-z_]+)\s*\(", src))
+    return sorted(names)
 
 
 def test_every_declared_symbol_is_exported(lib):
     names = declared()
     assert "rd_gradient" in names and "rd_hessvec" in names
+    assert "rg_gradient" in names and "rg_hessvec" in names and "rg_project" in names
     for name in names:
         assert hasattr(lib, name), name
 
@@ -62,3 +68,22 @@ def test_invalid_arguments_are_rejected(lib):
     assert lib.rd_workspace_size(ctypes.byref(cfg), 0, ctypes.byref(nb)) == 1
     assert lib.rd_gradient(None, None, 0.0, 0.0, None, None) == 1
     assert lib.rd_last_pcg_iters(None) == 0
+
+
+def test_registration_config_and_argument_checks(lib):
+    from paper_1907_07774_gb300 import rg as G
+    L = G.lib()
+    cfg = G.rg_config()
+    assert L.rg_config_default(ctypes.byref(cfg)) == 0
+    assert list(cfg.n) == [64, 64, 64] and cfg.nt == 8 and cfg.prec == G.RD_FP64 and cfg.beta_v == 1e-2
+    h = ctypes.c_void_p()
+    cfg.n[2] = 40
+    assert L.rg_create(ctypes.byref(h), ctypes.byref(cfg), None) == 2        # RD_ERR_SHAPE
+    cfg.n[2] = 64
+    cfg.nt = 0
+    assert L.rg_create(ctypes.byref(h), ctypes.byref(cfg), None) == 1        # RD_ERR_ARG
+    cfg.nt = 8
+    cfg.beta_v = 0.0
+    assert L.rg_create(ctypes.byref(h), ctypes.byref(cfg), None) == 1
+    assert not h.value
+    assert L.rg_gradient(None, None, None, None) == 1

@@ -37,3 +37,24 @@ def test_lattice_centred_and_spaced():
     assert c.shape == (27, 3)
     assert np.allclose(c.mean(axis=0), math.pi)
     assert np.allclose(np.unique(c[:, 2]) - math.pi, [-0.5, 0.0, 0.5])
+
+
+def test_trig_sum_on_the_grid_matches_direct_evaluation_and_curls_are_divergence_free():
+    import numpy as np
+    from paper_1907_07774_gb300 import synth
+    rng = np.random.default_rng(0)
+    n = (8, 16, 12)
+    X = synth.coords_mesh(n)
+    T = synth.TrigSum.random(rng, 3)
+    assert np.abs(T.grid(n) - T(X)).max() < 1e-12
+    for a in range(3):
+        assert np.abs(T.grid_deriv(n, a) - T.deriv(X, a)).max() < 1e-12
+    pots = [synth.TrigSum.random(rng, 3) for _ in range(3)]
+    v = synth.curl_field_grid(pots, n)
+    w = synth.curl_field(pots, X)
+    assert max(np.abs(a - b).max() for a, b in zip(v, w)) < 1e-12
+    # divergence of the curl through exact derivatives of its modes
+    k = [np.fft.fftfreq(m, 1.0 / m) for m in n]
+    V = [np.fft.fftn(x) for x in v]
+    D = sum(1j * k[a].reshape([-1 if b == a else 1 for b in range(3)]) * V[a] for a in range(3))
+    assert np.abs(np.fft.ifftn(D)).max() < 1e-10
