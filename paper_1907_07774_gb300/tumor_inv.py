@@ -523,12 +523,21 @@ def weighted_l2(solver, p0, k_f0, rho_f, beta, weights, invert_rho=False, k_f_sc
     """Weighted-l2 phase: L-BFGS + More-Thuente on
     ``D(p, k_f) + beta / 2 sum_i w_i p_i^2`` (Sec. 2.3, Sec. 3.1), k_f >= 0,
     optionally also rho_f.  Variables are scaled (k_f by ``k_f_scale``,
-    default ``max(k_f0, 1e-2)``).  Stops when the gradient norm falls below
+    default ``max(k_f0, 1e-2)``; ``"auto"``: the scale that gives k_f's
+    initial scaled gradient the root-mean-square size of the p components,
+    so that the first quasi-Newton steps move both).  Stops when the gradient norm falls below
     ``opttol`` times the reference gradient, by default the gradient at
     p = 0 (Sec. 3.1)."""
     npar = solver.np
     w = np.asarray(weights, dtype=np.float64)
-    ks = float(k_f_scale) if k_f_scale else max(abs(float(k_f0)), 1e-2)
+    if isinstance(k_f_scale, str) and k_f_scale == "auto":
+        p0v = np.asarray(p0, dtype=np.float64)
+        _, g0 = _gradient(solver, p0v, max(float(k_f0), 0.0), rho_f)
+        rms = math.sqrt(float(np.mean((g0[:npar] + beta * w * p0v) ** 2)))
+        gk = abs(float(g0[npar]))
+        ks = rms / gk if (gk > 0.0 and rms > 0.0) else max(abs(float(k_f0)), 1e-2)
+    else:
+        ks = float(k_f_scale) if k_f_scale else max(abs(float(k_f0)), 1e-2)
     rs = float(rho_scale) if rho_scale else max(abs(float(rho_f)), 1.0)
     nv = npar + (2 if invert_rho else 1)
     scale = np.ones(nv)
@@ -565,7 +574,7 @@ def weighted_l2(solver, p0, k_f0, rho_f, beta, weights, invert_rho=False, k_f_sc
 
 def tumor_inversion(solver, rho_f, k_f_l2=None, p0=None, target=0.95, beta_steps=6, gist_kw=None,
                     tau_s=0.1, w_large=1.0, w_small=0.0, beta_l2=1e-4, opttol=1e-3, l2_maxit=50,
-                    invert_rho=False, nonneg=True):
+                    invert_rho=False, nonneg=True, k_f_scale="auto"):
     """Both phases (Sec. 2.3): l1 with k_f = 0 and the Hoyer beta search,
     then weighted l2 on (p, k_f) from the l1 solution; ``k_f_l2`` is the
     starting diffusivity of the l2 phase (default 0)."""
@@ -576,7 +585,7 @@ def tumor_inversion(solver, rho_f, k_f_l2=None, p0=None, target=0.95, beta_steps
     w = l2_weights(l1.p, tau_s, w_large, w_small)
     kf0 = 0.0 if k_f_l2 is None else float(k_f_l2)
     l2, scale = weighted_l2(solver, l1.p, kf0, rho_f, beta_l2, w, invert_rho=invert_rho, opttol=opttol,
-                            maxit=l2_maxit, nonneg=nonneg)
+                            maxit=l2_maxit, nonneg=nonneg, k_f_scale=k_f_scale)
     th = l2.x * scale
     rf = th[npar + 1] if invert_rho else rho_f
     return TumorInversionResult(p=th[:npar], k_f=max(th[npar], 0.0), rho_f=rf, misfit=l2.f, beta_l1=l1.beta,

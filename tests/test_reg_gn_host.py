@@ -63,3 +63,10 @@ def test_gauss_newton_recovers_most_of_a_known_transport():
     cosang = sum(float(np.vdot(a, b)) for a, b in zip(res.v, prob.v)) / math.sqrt(
         sum(float(np.vdot(a, a)) for a in res.v) * sum(float(np.vdot(b, b)) for b in prob.v))
     assert cosang > 0.7
+
+
+def test_beta_continuation_schedule():
+    from paper_1907_07774_gb300.picard import beta_schedule
+    s = beta_schedule(1e-1, 1e-3, final_repeats=2)
+    assert np.allclose(s, [1e-1, 1e-2, 1e-3, 1e-3])
+    assert beta_schedule(1e-3, 1e-3, final_repeats=2) == [1e-3, 1e-3]

@@ -334,3 +334,23 @@ def test_lbfgs_keeps_p_nonnegative_by_default():
     free = th[:10] > 0
     assert np.max(np.abs(g[:10][free])) <= 1e-6 * np.linalg.norm(G.T @ b)
     assert np.all(g[:10][~free] >= -1e-9)
+
+
+def test_auto_k_f_scaling_moves_a_weakly_coupled_diffusivity():
+    """When dJ/dk_f is tiny next to dJ/dp, the automatic scale lets the
+    first quasi-Newton steps move k_f: within a few iterations it gets much
+    closer to the ridge optimum than with the fixed scale."""
+    G, b, x = _sparse_problem(m=50, n=12, k=3, seed=16)
+    u = 1e-3 * np.random.default_rng(17).standard_normal(50)
+    kf_true = 40.0
+    s = FakeSolver(G, b + kf_true * u, u=u)
+    w = np.ones(12)
+    beta = 1e-3
+    M = np.column_stack([G, u])
+    want = np.linalg.solve(M.T @ M + np.diag(np.concatenate([beta * w, [0.0]])), M.T @ (b + kf_true * u))
+    errs = {}
+    for ks in (None, "auto"):
+        res, scale = T.weighted_l2(s, np.zeros(12), 1.0, 0.0, beta, w, opttol=1e-12, maxit=6, nonneg=False,
+                                   k_f_scale=ks)
+        errs[ks] = abs((res.x * scale)[12] - want[12])
+    assert errs["auto"] < 0.1 * errs[None], errs
