@@ -184,6 +184,33 @@ struct RegEngine final : RegBase {
     })
   }
 
+  // three derivatives along `axis` in one pass (see Deriv3Mode)
+  cudaError_t deriv3(int mode, int axis, T* const* u, T* const* w, T* const* out, double cc) {
+    Deriv3Args<T> a{};
+    for (int k = 0; k < 3; ++k) {
+      a.u[k] = u[k];
+      a.w[k] = w[k];
+      a.out[k] = out[k];
+    }
+    a.c = cc;
+    a.axis = axis;
+    a.g = g;
+    const int Ln = g.n[axis];
+    a.twA = twA[lidx(Ln)];
+    a.twB = twB[lidx(Ln)];
+    const long long npairs = nn / Ln / 2;
+    RD_DISPATCH_L(Ln, {
+      constexpr size_t sm = detail::pencil_smem<T, LL>();
+      const long long blocks = (npairs + Shape<LL>::G - 1) / Shape<LL>::G;
+      const bool ct = (axis == 2);
+      if (mode == kD3Body)
+        return ct ? detail::launch_pencil(k_deriv3<T, LL, true, kD3Body>, sm, blocks, a, stream)
+                  : detail::launch_pencil(k_deriv3<T, LL, false, kD3Body>, sm, blocks, a, stream);
+      return ct ? detail::launch_pencil(k_deriv3<T, LL, true, kD3Src>, sm, blocks, a, stream)
+                : detail::launch_pencil(k_deriv3<T, LL, false, kD3Src>, sm, blocks, a, stream);
+    })
+  }
+
   cudaError_t hartley(int axis, const T* in, T* out) {
     DhtArgs<T> a{};
     a.in = in;
@@ -362,9 +389,11 @@ struct RegEngine final : RegBase {
         for (int k = 0; k < 3; ++k) std::swap(lam[k], lam2[k]);
       }
       const double wj = dt * ((j == 0 || j == cfg.nt) ? 0.5 : 1.0);
-      for (int a = 0; a < 3; ++a)
-        for (int k = 0; k < 3; ++k)
-          if ((e = deriv(kDerMulAdd, a, 1, L3(j, k), lam[k], b[a], wj)) != cudaSuccess) return e;
+      T* mj[3] = {L3(j, 0), L3(j, 1), L3(j, 2)};
+      for (int a = 0; a < 3; ++a) {
+        T* ba[3] = {b[a], b[a], b[a]};
+        if ((e = deriv3(kD3Body, a, mj, lam, ba, wj)) != cudaSuccess) return e;
+      }
     }
     return leray(b, out);
   }
@@ -418,10 +447,12 @@ struct RegEngine final : RegBase {
   // s_k = grad(m_k^j) . vt
   cudaError_t source(int j, T* const* s) {
     cudaError_t e;
-    for (int k = 0; k < 3; ++k) {
+    for (int k = 0; k < 3; ++k)
       if ((e = cudaMemsetAsync(s[k], 0, sizeof(T) * nn, stream)) != cudaSuccess) return e;
-      for (int a = 0; a < 3; ++a)
-        if ((e = deriv(kDerMulAdd, a, 1, L3(j, k), vt[a], s[k], 1.0)) != cudaSuccess) return e;
+    T* mj[3] = {L3(j, 0), L3(j, 1), L3(j, 2)};
+    for (int a = 0; a < 3; ++a) {
+      T* wa[3] = {vt[a], vt[a], vt[a]};
+      if ((e = deriv3(kD3Src, a, mj, wa, s, 1.0)) != cudaSuccess) return e;
     }
     return cudaSuccess;
   }

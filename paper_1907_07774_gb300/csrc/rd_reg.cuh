@@ -51,7 +51,9 @@ __device__ __forceinline__ void interp(const T* const* u, const Geom& g, T X0, T
 #pragma unroll
       for (int k = 0; k < K; ++k) {
         const T* p = u[k] + row;
-        const T acc = w2[0] * p[i2[0]] + w2[1] * p[i2[1]] + w2[2] * p[i2[2]] + w2[3] * p[i2[3]];
+        // read-only path: the gathered fields are never written by this kernel
+        const T acc = w2[0] * __ldg(p + i2[0]) + w2[1] * __ldg(p + i2[1]) + w2[2] * __ldg(p + i2[2]) +
+                      w2[3] * __ldg(p + i2[3]);
         out[k] += w01 * acc;
       }
     }
@@ -202,6 +204,63 @@ __global__ void __launch_bounds__(kThreads) k_deriv(DerivArgs<T> a) {
           o = {o.x + p.x, o.y + p.y};
         }
         st2<T, CONTIG>(a.out, b0, b1, off, o);
+      }
+    }
+  }
+}
+
+// Three first derivatives along `axis` in one pass (three transforms per
+// pencil pair, one read-modify-write of the outputs):
+//   kD3Body: out[0] += c sum_k w[k] d u[k]      (body force sum_i l_i d_a m_i)
+//   kD3Src:  out[k] += c w[0] d u[k], k = 0..2   (source grad(m_k) . v~, axis term)
+enum Deriv3Mode { kD3Body = 0, kD3Src = 1 };
+
+template <typename T>
+struct Deriv3Args {
+  const T* u[3];
+  const T* w[3];
+  T* out[3];
+  double c;
+  int axis;
+  Geom g;
+  const cpx<T>* twA;
+  const cpx<T>* twB;
+};
+
+template <typename T, int L, bool CONTIG, int MODE>
+__global__ void __launch_bounds__(kThreads) k_deriv3(const __grid_constant__ Deriv3Args<T> a) {
+  using Sh = Shape<L>;
+  constexpr int R = Sh::R, TH = Sh::TH, G = Sh::G;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int g = threadIdx.x / TH, t = threadIdx.x % TH;
+  cpx<T>* sm = reinterpret_cast<cpx<T>*>(smraw) + g * Sh::GSTRIDE;
+  const long long npairs = a.g.nn / L / 2;
+  const T c = T(a.c / double(L));
+  for (long long base = (long long)blockIdx.x * G; base < npairs; base += (long long)gridDim.x * G) {
+    const long long pair = base + g;
+    const bool act = pair < npairs;
+    long long b0, b1, st;
+    pair_addr<CONTIG>(a.g, a.axis, act ? pair : 0, b0, b1, st);
+#pragma unroll 1
+    for (int k = 0; k < 3; ++k) {
+      cpx<T> v[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+        v[r] = act ? ld2<T, CONTIG>(a.u[k], b0, b1, (long long)idx_a<L>(r, t) * st) : cpx<T>{T(0), T(0)};
+      fft_ab<T, L, -1>(v, sm, t, a.twA);
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[r] = times_ik(v[r], kwave<L>(idx_b<L>(r, t)));
+      fft_ba<T, L, +1>(v, sm, t, a.twB);
+      if (act) {
+        const T* w = a.w[MODE == kD3Body ? k : 0];
+        T* out = a.out[MODE == kD3Body ? 0 : k];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const long long off = (long long)idx_a<L>(r, t) * st;
+          const cpx<T> wv = ld2<T, CONTIG>(w, b0, b1, off);
+          const cpx<T> p = ld2<T, CONTIG>(out, b0, b1, off);
+          st2<T, CONTIG>(out, b0, b1, off, {p.x + c * wv.x * v[r].x, p.y + c * wv.y * v[r].y});
+        }
       }
     }
   }

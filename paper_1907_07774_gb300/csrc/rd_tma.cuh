@@ -423,7 +423,7 @@ struct DhtTmaArgs {
 // Hartley pass along a strided axis: MODE kDhtPlain (out = H in, written at
 // layout-B positions of each pencil) or kDhtSym (out = H S' H in, rz reduced).
 template <typename T, int L, int AXIS, int MODE>
-__global__ void __launch_bounds__(TmaShape<T, L>::THREADS) k_dht_tma(const __grid_constant__ DhtTmaArgs<T> a) {
+__global__ void __launch_bounds__(TmaShape<T, L>::THREADS, (MODE == kDhtSym && sizeof(T) == 4) ? 4 : 1) k_dht_tma(const __grid_constant__ DhtTmaArgs<T> a) {
   using S = TmaShape<T, L>;
   constexpr int R = S::R, TH = S::TH, TB = S::TILE_BYTES;
   extern __shared__ __align__(16) unsigned char smem_raw[];
