@@ -5,7 +5,8 @@ Newton step from conjugate gradients on the Gauss-Newton Hessian
 (``rd_hessvec``; forcing term ``eta = min(0.5, sqrt(|g| / |g_0|))`` after
 Eisenstat-Walker, at most ``cg_maxit`` products), and a projected Armijo
 backtracking line search on the misfit (``rd_forward``) that keeps
-``k_f >= 0``.  This is the inexact
+``k_f >= 0``; a trial whose solve turns non-finite counts as a rejected
+step.  This is the inexact
 Gauss-Newton-Krylov / PCG / Armijo scheme of Sec. 3.2 applied to the tumor
 parameters.  The reduction scalars (CG inner products, step lengths,
 sufficient-decrease tests) are FP64 on the host over the n_p + 2 parameters;
@@ -14,6 +15,7 @@ every field operation runs in the CUDA library.
 
 from __future__ import annotations
 
+import math
 import time
 from dataclasses import dataclass, field
 
@@ -106,7 +108,14 @@ def gauss_newton(solver, theta0, iters=10, cg_maxit=20, armijo_c=1e-4, max_backt
             trial = project(theta + step * d)
             n_ls += 1
             if np.all(np.isfinite(trial)):
-                Jt = solver.rd_forward(*split(trial))
+                try:
+                    Jt = solver.rd_forward(*split(trial))
+                except Exception as exc:
+                    # a trial whose solve turns non-finite (RD_ERR_NONFINITE) is a
+                    # rejected step, not a failure of the run
+                    if getattr(exc, "status", None) != 6:
+                        raise
+                    Jt = math.inf
                 # projected Armijo condition: sufficient decrease along the
                 # actual (projected) displacement
                 if Jt <= J + armijo_c * float(g @ (trial - theta)):

@@ -79,3 +79,33 @@ def test_line_search_keeps_k_f_nonnegative():
                         lambda th: np.eye(3), 1)
     res = gn.gauss_newton(prob, np.array([0.0, 0.5, 0.0]), iters=5, cg_maxit=5)
     assert res.theta[1] >= 0.0
+
+
+class _NonFinite(RuntimeError):
+    status = 6
+
+
+def test_non_finite_trial_solves_are_rejected_steps():
+    """A full Newton step that makes the solve blow up (as a negative
+    initial concentration does) is halved instead of ending the run."""
+    rng = np.random.default_rng(2)
+    A = rng.standard_normal((20, 5))
+    want = np.array([0.3, -0.2, 0.5, 0.05, 7.0])
+    b = A @ want
+    base = LeastSquares(lambda th: A @ th - b, lambda th: A, 3)
+    th0 = np.array([0.1, 0.2, 0.3, 0.4, 0.5])
+
+    class Fragile(LeastSquares):
+        calls = 0
+
+        def rd_forward(self, p, k_f, rho_f):
+            Fragile.calls += 1
+            if Fragile.calls == 2:          # the first line-search trial
+                raise _NonFinite("non-finite value in a PCG solve")
+            return super().rd_forward(p, k_f, rho_f)
+
+    prob = Fragile(base.r, base.jac, 3)
+    J0 = base.rd_forward(th0[:3], th0[3], th0[4])
+    res = gn.gauss_newton(prob, th0, iters=30, cg_maxit=20)
+    assert res.history[0]["step"] == 0.5 and res.history[0]["line_search"] == 2
+    assert res.misfit < 1e-6 * J0
