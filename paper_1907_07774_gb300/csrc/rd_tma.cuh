@@ -679,29 +679,33 @@ __global__ void __launch_bounds__(TmaRowShape<T, L>::THREADS) k_pcg_opx_tma(cons
       prow_a[n] = v[r].x;
       prow_b[n] = v[r].y;
     }
-    fft_ba<T, L, -1, true>(v, sm, t, twB);
+    // d(kappa d p): the two derivative applications share one copy of the
+    // transform code (a loop that is not unrolled keeps the kernel small
+    // enough for the instruction cache)
+#pragma unroll 1
+    for (int pass = 0; pass < 2; ++pass) {
+      fft_ba<T, L, -1, true>(v, sm, t, twB);
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = times_ik(v[r], kwave<L>(idx_a<L>(r, t)));
-    fft_ab<T, L, +1, true>(v, sm, t, twA);
-    ok = mbar_wait(&kbar, i & 1);
-    if (__syncthreads_or(!ok)) { bad = true; break; }
-    ++pk.done;
+      for (int r = 0; r < R; ++r) v[r] = times_ik(v[r], kwave<L>(idx_a<L>(r, t)));
+      fft_ab<T, L, +1, true>(v, sm, t, twA);
+      if (pass == 1) break;
+      ok = mbar_wait(&kbar, i & 1);
+      if (__syncthreads_or(!ok)) { bad = true; break; }
+      ++pk.done;
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const int n = idx_b<L>(r, t);
-      const T ka = *row_elem<T, L>(k_buf, ra, n), kb = *row_elem<T, L>(k_buf, rb, n);
-      lk += ka * v[r].x * v[r].x + kb * v[r].y * v[r].y;
-      v[r].x *= ka;
-      v[r].y *= kb;
+      for (int r = 0; r < R; ++r) {
+        const int n = idx_b<L>(r, t);
+        const T ka = *row_elem<T, L>(k_buf, ra, n), kb = *row_elem<T, L>(k_buf, rb, n);
+        lk += ka * v[r].x * v[r].x + kb * v[r].y * v[r].y;
+        v[r].x *= ka;
+        v[r].y *= kb;
+      }
+      red_pp += double(lpp);
+      red_k += double(lk);
+      __syncthreads();   // every kappa value is in registers
+      if (threadIdx.x == 0 && more) issue(k_buf, &a.map_k, &kbar, pk, tile + stride);
     }
-    red_pp += double(lpp);
-    red_k += double(lk);
-    __syncthreads();   // every kappa value is in registers
-    if (threadIdx.x == 0 && more) issue(k_buf, &a.map_k, &kbar, pk, tile + stride);
-    fft_ba<T, L, -1, true>(v, sm, t, twB);
-#pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = times_ik(v[r], kwave<L>(idx_a<L>(r, t)));
-    fft_ab<T, L, +1, true>(v, sm, t, twA);
+    if (bad) break;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const int n = idx_b<L>(r, t);
