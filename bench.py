@@ -47,6 +47,23 @@ def env_rank():
         int(os.environ.get("LOCAL_RANK", "0"))
 
 
+def max_over_ranks(x, dist=None, device="cuda"):
+    """The largest value of x over all ranks (the slowest rank's time); x
+    itself on a single process."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, world, ms_max):
+    """Whole-job throughput of independent replicas (weak scaling): the
+    units every rank processed, divided by the slowest rank's time."""
+    return world * units_per_rank / (ms_max / 1e3)
+
+
 def problem(n, nt):
     from paper_1907_07774_gb300 import synth
     return synth.calibration_problem(n=n, nt=nt, m=5)
@@ -252,14 +269,10 @@ def run_ours(args, rank, world, local):
             J, g = ctx.rd_gradient(p, k_f, rho_f)
         e1.record(stream)
         barrier()
-    ms = e0.elapsed_time(e1)
+    ms = max_over_ranks(e0.elapsed_time(e1), dist)
     clocks = clk.summary()
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
     cells = n ** 3 * nt
-    value = world * cells * args.steps / (ms / 1e3)
+    value = job_rate(cells * args.steps, world, ms)
 
     # ---- one more step of the same workload with every launch bracketed by
     # CUDA events on the solver's stream (host-driven PCG loop, same kernels)
@@ -303,12 +316,8 @@ def run_ours(args, rank, world, local):
         Je, ge = ctx.rd_gradient(p, k_f, rho_f)
     e3.record(stream)
     barrier()
-    ms_e2e = e2.elapsed_time(e3)
-    if dist is not None:
-        t = torch.tensor([ms_e2e], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_e2e = float(t.item())
-    e2e = {"value": world * cells * args.steps / (ms_e2e / 1e3), "unit": UNIT,
+    ms_e2e = max_over_ranks(e2.elapsed_time(e3), dist)
+    e2e = {"value": job_rate(cells * args.steps, world, ms_e2e), "unit": UNIT,
            "h2d_bytes_per_step": 4 * n ** 3 * 8 + len(p) * 8,
            "d2h_bytes_per_step": (len(p) + 2) * 8 + 8}
 
