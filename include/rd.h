@@ -14,7 +14,8 @@
  * splitting with the exact logistic reaction step and Crank-Nicolson
  * diffusion).  The Crank-Nicolson system (I - tau/2 A) x = b is solved by
  * preconditioned CG with the spectral constant-coefficient preconditioner
- * 1 / (1 + tau/2 * mean(kappa) * |k|^2).
+ * 1 / (1 + tau/2 * kbar * |k|^2), kbar the mean of kappa over the voxels
+ * where it is positive.
  *
  * Plain C ABI: host or device pointers and sizes only.  One context drives
  * one grid on the current CUDA device and one stream.
@@ -176,7 +177,8 @@ rd_status rd_batch_gradient(rd_ctx* const* ctxs, int count, const double* const*
 /* Building blocks, exposed for testing and for callers composing their own
  * solvers.  Au = k_f div(kappa1 grad u) with the Fourier pseudo-spectral
  * derivatives of Sec. 3.3 (i k zeroed at the Nyquist index); z = M^-1 r with
- * M^-1 = F^-1 diag(1 / (1 + tau/2 k_f mean(kappa1) |k|^2)) F, the PCG
+ * M^-1 = F^-1 diag(1 / (1 + tau/2 k_f kbar1 |k|^2)) F (kbar1 the mean of
+ * kappa1 where it is positive), the PCG
  * preconditioner.  Fields FP64, host or device; needs rd_set_tissue. */
 rd_status rd_apply_operator(rd_ctx* ctx, double k_f, const double* u, double* Au);
 rd_status rd_apply_precond(rd_ctx* ctx, double k_f, const double* r, double* z);
@@ -186,7 +188,7 @@ rd_status rd_apply_precond(rd_ctx* ctx, double k_f, const double* r, double* z);
  * it: applications whose device memory belongs to another framework's pool,
  * and latency-critical loops that must not pay cudaMalloc's implicit device
  * synchronisation).  Computes z = F^-1 [F r / (1 + coef |k~|^2)] (the PCG
- * preconditioner above with coef = tau/2 k_f mean(kappa1)) for FP64 device
+ * preconditioner above with coef = tau/2 k_f kbar1) for FP64 device
  * fields r and z on grid n[0] x n[1] x n[2] (each a power of two from 8 to 256,
  * or 96;
  * RD_ERR_SHAPE otherwise), ordered on `stream`.  No context, no workspace: the

@@ -32,7 +32,8 @@ Readings where the paper is silent (each also listed in the design doc):
 * Strang order ``L(tau/2) CN(tau) L(tau/2)`` with ``L_t`` the exact logistic
   flow ``c e^{rho t} / (1 - c + c e^{rho t})``.
 * CN: ``(I - tau/2 A) c** = (I + tau/2 A) c*`` solved by PCG with the
-  spectral preconditioner ``1 / (1 + tau/2 * mean(kappa) * |k~|^2)``.
+  spectral preconditioner ``1 / (1 + tau/2 * kbar * |k~|^2)``, kbar the
+  mean of kappa over the voxels where it is positive (the brain region).
 * ``i k`` is zeroed at the Nyquist index of every even axis (``k~``), which
   keeps ``A = div(kappa grad .)`` real, symmetric and negative semidefinite.
 * Adjoint reaction sign: the adjoint of the logistic step is multiplication
@@ -154,6 +155,13 @@ def pcg(matvec, precond, b, x0, rtol, maxit):
     return x, it, rn / bn
 
 
+def kbar_positive(kappa1):
+    """Preconditioner constant: the mean of kappa1 over the voxels where it
+    is positive (0 if there are none)."""
+    pos = kappa1[kappa1 > 0.0]
+    return float(pos.mean()) if pos.size else 0.0
+
+
 # --------------------------------------------------------------------------
 # Gaussian basis Phi (Eq. tumor:fwd-init)
 # --------------------------------------------------------------------------
@@ -227,7 +235,7 @@ class Model:
     def solve(self, b, x0, k_f):
         """``(I - s A) x = b`` by PCG with the spectral preconditioner."""
         s = self.s
-        coef = s * k_f * float(np.mean(self.kappa1))
+        coef = s * k_f * kbar_positive(self.kappa1)
         x, it, _ = pcg(lambda v: v - s * self.A(v, k_f),
                        lambda r: self.sp.precond(r, coef),
                        b, x0, self.rtol, self.maxit)

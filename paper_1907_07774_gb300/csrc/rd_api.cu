@@ -986,7 +986,7 @@ struct Engine : EngineBase {
     a.rw1 = cfg.rho_w[1];
     a.rw2 = cfg.rho_w[2];
     a.nn = nn;
-    a.fin = fin(kFinSet, 0, 1.0 / double(nn), &prm->kbar1);
+    a.fin = fin(kFinRatio, 0, 1.0, &prm->kbar1);   // mean of kappa1 where it is positive
     if ((e = L_::coef(a, stream)) != cudaSuccess) return cuda_fail(e, "coefficients");
     if (cfg.moving_atlas)
       for (int j = 0; j < 3; ++j)

@@ -84,7 +84,8 @@ enum FinKind {
   kFinRr,       // residual norm, iteration count, convergence
   kFinSet,      // *target = scale * total
   kFinPqAdd,    // pq_part += [tot0] + scale s k_f tot_last   (p.p and kappa |d p|^2 terms)
-  kFinPqLast    // pq = pq_part + scale s k_f tot; alpha = rz / pq
+  kFinPqLast,   // pq = pq_part + scale s k_f tot; alpha = rz / pq
+  kFinRatio     // *target = total_0 / total_1 (0 when total_1 == 0)
 };
 
 struct Fin {
@@ -175,6 +176,9 @@ __device__ __forceinline__ void finalize(const Fin& f, const double* tots, int K
       break;
     case kFinSet:
       *f.target = f.scale * tot;
+      break;
+    case kFinRatio:
+      *f.target = (K > 1 && tots[1] > 0.0) ? tots[0] / tots[1] : 0.0;
       break;
     default:
       break;

@@ -616,17 +616,20 @@ struct CoefArgs {
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_coef(CoefArgs<T> a) {
-  double red = 0.0;
+  double red = 0.0, cnt = 0.0;
   for (long long i = (long long)blockIdx.x * kThreads + threadIdx.x; i < a.nn;
        i += (long long)gridDim.x * kThreads) {
     const double x0 = a.m0[i], x1 = a.m1[i], x2 = a.m2[i];
     const double k = a.kw0 * x0 + a.kw1 * x1 + a.kw2 * x2;
     a.kappa1[i] = T(k);
     a.rho1[i] = T(a.rw0 * x0 + a.rw1 * x1 + a.rw2 * x2);
-    red += double(T(k));
+    if (k > 0.0) {
+      red += double(T(k));
+      cnt += 1.0;
+    }
   }
-  double vv[1] = {red};
-  reduce_finish<1>(vv, a.fin);
+  double vv[2] = {red, cnt};
+  reduce_finish<2>(vv, a.fin);
 }
 
 // out = ca qk + cb qr in FP64 (coupling field of one tissue class)
