@@ -181,6 +181,13 @@ rd_status rd_batch_gradient(rd_ctx* const* ctxs, int count, const double* const*
  * kappa1 where it is positive), the PCG
  * preconditioner.  Fields FP64, host or device; needs rd_set_tissue. */
 rd_status rd_apply_operator(rd_ctx* ctx, double k_f, const double* u, double* Au);
+
+/* Tuning of the PCG preconditioner (this implementation's choice; the paper
+ * names no preconditioner): kbar1 := scale * (mean of kappa1 over the
+ * voxels where it is positive).  Default 1; kept across rd_set_tissue.
+ * Changes only the convergence of the PCG solves, not what they converge
+ * to.  RD_ERR_ARG unless scale > 0 and finite. */
+rd_status rd_set_precond_scale(rd_ctx* ctx, double scale);
 rd_status rd_apply_precond(rd_ctx* ctx, double k_f, const double* r, double* z);
 
 /* Allocation-free preconditioner application (the paper has no counterpart;

@@ -218,6 +218,7 @@ struct EngineBase {
   virtual rd_status set_basis(const double*, double) = 0;
   virtual rd_status set_data(const double*) = 0;
   virtual rd_status set_anatomy_data(const double*, const double*, const double*) = 0;
+  virtual rd_status set_precond_scale(double) = 0;
   virtual rd_status coupling_field(double*, double*, double*) = 0;
   virtual rd_status forward(const double*, double, double, double*, double*) = 0;
   virtual rd_status adjoint(double*) = 0;
@@ -254,6 +255,7 @@ struct Engine : EngineBase {
   T* qf[kCouplingFields] = {};    // coupling integrands (cfg.coupling)
   bool have_q = false;
   double q_kf = 0.0, q_rho = 0.0;
+  double kbar_base = 0.0, kbar_factor = 1.0;   // preconditioner constant and its user scale
   std::vector<T*> slots;   // checkpoint storage
   int nmax = 0;
   double sigma = 0;
@@ -995,7 +997,12 @@ struct Engine : EngineBase {
         cudaSuccess)
       return cuda_fail(e, "read kbar");
     if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_fail(e, "sync");
+    kbar_base = hprm->kbar1;
     have_tissue = true;
+    if (kbar_factor != 1.0) {
+      rd_status s = set_precond_scale(kbar_factor);
+      if (s != RD_OK) return s;
+    }
     have_traj = false;
     have_q = false;
     return RD_OK;
@@ -1035,6 +1042,18 @@ struct Engine : EngineBase {
     if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_fail(e, "sync");
     have_mdata = true;
     have_q = false;
+    return RD_OK;
+  }
+
+  // kbar1 = kbar_base * scale, on the host copy (uploaded with the
+  // parameters) and on the device (read by the PCG graphs at run time)
+  rd_status set_precond_scale(double scale) override {
+    kbar_factor = scale;
+    if (!have_tissue) return RD_OK;
+    hprm->kbar1 = kbar_base * scale;
+    cudaError_t e = cudaMemcpyAsync(&prm->kbar1, &hprm->kbar1, sizeof(double), cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) return cuda_fail(e, "preconditioner scale");
     return RD_OK;
   }
 
@@ -1462,6 +1481,11 @@ rd_status rd_hessvec(rd_ctx* c, const double* p, double k_f, double rho_f, const
 rd_status rd_apply_operator(rd_ctx* c, double k_f, const double* u, double* Au) {
   if (!c || !u || !Au || !std::isfinite(k_f)) return RD_ERR_ARG;
   return c->e->apply_operator(k_f, u, Au);
+}
+
+rd_status rd_set_precond_scale(rd_ctx* c, double scale) {
+  if (!c || !(scale > 0.0) || !std::isfinite(scale)) return RD_ERR_ARG;
+  return c->e->set_precond_scale(scale);
 }
 
 rd_status rd_apply_precond(rd_ctx* c, double k_f, const double* r, double* z) {

@@ -61,6 +61,7 @@ def lib():
         "rd_hessvec": ([vp, vp, cd, cd, vp, vp], st),
         "rd_apply_operator": ([vp, cd, vp, vp], st),
         "rd_apply_precond": ([vp, cd, vp, vp], st),
+        "rd_set_precond_scale": ([vp, cd], st),
         "rd_last_pcg_iters": ([vp], ci),
         "rd_last_pcg_solves": ([vp], ci),
         "rd_last_graph_solves": ([vp], ci),
@@ -221,6 +222,9 @@ class Context:
         (a, ka), (b, kb), (c, kc) = _ptr(q_wm), _ptr(q_gm), _ptr(q_csf)
         self._call(lib().rd_coupling_field(self.h, a, b, c))
         return q_wm, q_gm, q_csf
+
+    def rd_set_precond_scale(self, scale):
+        self._call(lib().rd_set_precond_scale(self.h, float(scale)))
 
     def rd_set_anatomy_data(self, md_wm, md_gm, md_csf):
         (a, ka), (b, kb), (c, kc) = _ptr(md_wm), _ptr(md_gm), _ptr(md_csf)

@@ -469,3 +469,23 @@ def test_autotuned_grid_sizes_keep_parity():
         assert rel(g, g_or) <= TOL["mixed"] and abs(J - J_or) <= TOL["mixed"] * J_or
     finally:
         R.rd_autotune_clear()
+
+
+def test_preconditioner_scale_changes_convergence_not_the_result():
+    prob, M, d = _grad_case(nt=4)
+    J_or, g_or, _, _ = M.gradient(prob.p, prob.k_f, prob.rho_f, d)
+    ctx = gpu_for(prob, "fp64")
+    ctx.rd_set_data(d)
+    ctx.rd_gradient(prob.p, prob.k_f, prob.rho_f)
+    it1 = ctx.rd_last_pcg_iters()
+    for scale in (0.3, 3.0):
+        ctx.rd_set_precond_scale(scale)
+        J, g = ctx.rd_gradient(prob.p, prob.k_f, prob.rho_f)
+        assert abs(J - J_or) <= 1e-10 * abs(J_or) and rel(g, g_or) <= 1e-10
+        assert ctx.rd_last_pcg_iters() != it1
+    ctx.rd_set_precond_scale(1.0)
+    ctx.rd_set_tissue(prob.m_wm, prob.m_gm, prob.m_csf)
+    ctx.rd_gradient(prob.p, prob.k_f, prob.rho_f)
+    assert ctx.rd_last_pcg_iters() == it1
+    with pytest.raises(RuntimeError):
+        ctx.rd_set_precond_scale(0.0)
