@@ -39,7 +39,7 @@ UNIT = "cell-updates/s"
 FALLBACK_HBM_GBS = 6800.0
 # PCG work of one FP64 gradient of this workload (rtol 1e-10), measured on
 # the GPU FP64 path; used to scale the CPU oracle sample in the reference arm.
-FP64_WORK = {"iters": 1474, "solves": 64}
+FP64_WORK = {"iters": 1322, "solves": 64}
 
 
 def env_rank():

@@ -70,7 +70,9 @@ typedef struct {
   double t_end;      /* final time (1.0 in the normalised model)             */
   int prec;          /* RD_FP64: all FP64.  RD_MIXED: fields in FP32,
                         reductions, norms and scalars in FP64               */
-  double pcg_rtol;   /* stop when ||r|| <= pcg_rtol ||f|| (f: rhs of the
+  double pcg_rtol;   /* state and adjoint solves stop when ||r|| <= pcg_rtol ||b||,
+                        b the right-hand side of the Crank-Nicolson system;
+                        tangent-linear solves when ||r|| <= pcg_rtol ||f|| (f: rhs of the
                         increment system (I - tau/2 A) dx = f, dx0 = 0)      */
   int pcg_maxit;
   int ckpt_stride;   /* 0: keep every step's state for the adjoint;

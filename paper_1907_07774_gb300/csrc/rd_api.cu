@@ -713,6 +713,18 @@ struct Engine : EngineBase {
     }
   }
 
+  // st->bb = ||x + cy y||^2: the Crank-Nicolson right-hand side of the next
+  // solve (forward: b = c* + f / 2 with f = 2 s A c*; adjoint: b = alpha**)
+  cudaError_t rhs_norm(const T* x, const T* y, double cy) {
+    NormArgs<T> a{};
+    a.x = x;
+    a.y = y;
+    a.cy = cy;
+    a.nn = nn;
+    a.fin = fin(kFinSet, 0, 1.0, &st->bb);
+    return L_::normsq(a, stream);
+  }
+
   rd_status fwd_step(int n) {
     cudaError_t e;
     rd_status rs;
@@ -725,6 +737,7 @@ struct Engine : EngineBase {
     a.out0 = f[F_CS];
     if ((e = L_::pw(kPwFwdPre, a, stream)) != cudaSuccess) return cuda_fail(e, "fwd pre");
     if ((e = apply3(f[F_CS], f[F_R], 2.0, 1)) != cudaSuccess) return cuda_fail(e, "fwd rhs");
+    if ((e = rhs_norm(f[F_CS], f[F_R], 0.5)) != cudaSuccess) return cuda_fail(e, "fwd rhs norm");
     if ((rs = pcg()) != RD_OK) return rs;
     PwArgs<T> b = pw_args();
     b.a = f[F_CS];
@@ -850,6 +863,7 @@ struct Engine : EngineBase {
     a.fin = fin(kFinAcc, kAccGrho, gscale);
     if ((e = L_::pw(kPwAdjPre, a, stream)) != cudaSuccess) return cuda_fail(e, "adj pre");
     if ((e = apply3(f[F_AB], f[F_R], 1.0, 1)) != cudaSuccess) return cuda_fail(e, "adj rhs");
+    if ((e = rhs_norm(f[F_AB], nullptr, 0.0)) != cudaSuccess) return cuda_fail(e, "adj rhs norm");
     if ((rs = pcg()) != RD_OK) return rs;
     for (int axis : {2, 1, 0}) {
       GradArgs<T> ga{};
@@ -1317,6 +1331,8 @@ struct Engine : EngineBase {
       a.out1 = f[F_U];
       if ((e = L_::pw(kPwTlPre, a, stream)) != cudaSuccess) return cuda_fail(e, "tl pre");
       if ((e = apply3(f[F_U], f[F_R], 1.0, 0)) != cudaSuccess) return cuda_fail(e, "tl rhs");
+      // tangent-linear solves stop relative to the increment right-hand side
+      if ((e = cudaMemsetAsync(&st->bb, 0, sizeof(double), stream)) != cudaSuccess) return cuda_fail(e, "tl");
       if ((s = pcg()) != RD_OK) return s;
       PwArgs<T> b = pw_args();
       b.a = f[F_CHS];

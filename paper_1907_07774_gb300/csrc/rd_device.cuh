@@ -39,6 +39,8 @@ struct Geom {
 // iteration can run without host round trips.
 struct PcgState {
   double ff;      // ||f||^2, f = right-hand side of the increment system
+  double bb;      // ||b||^2, b = right-hand side of the Crank-Nicolson system
+                  // (0: the stopping test uses ff)
   double rr;      // ||r||^2
   double rz;      // (r, M^-1 r)
   double pq;      // (p, (I - sA) p)
@@ -165,7 +167,7 @@ __device__ __forceinline__ void finalize(const Fin& f, const double* tots, int K
       } else if (!isfinite(tot)) {
         st->done = 1;
         st->status = kStNonFinite;
-      } else if (tot <= st->rtol2 * st->ff) {
+      } else if (tot <= st->rtol2 * (st->bb > 0.0 ? st->bb : st->ff)) {
         st->done = 1;
       } else if (st->it >= st->maxit || !(st->pq > 0.0)) {
         st->done = 1;

@@ -45,6 +45,7 @@ struct Launch {
   static cudaError_t to_f64(const T* in, double* out, long long nn, double scale, cudaStream_t s);
   static cudaError_t combine(const T* qk, const T* qr, double ca, double cb, double* out, long long nn,
                              cudaStream_t s);
+  static cudaError_t normsq(const NormArgs<T>& a, cudaStream_t s);
 };
 
 extern template struct Launch<float>;

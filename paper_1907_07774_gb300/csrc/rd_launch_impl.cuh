@@ -356,6 +356,11 @@ cudaError_t Launch<T>::to_f64(const T* in, double* out, long long nn, double sca
 }
 
 template <typename T>
+cudaError_t Launch<T>::normsq(const NormArgs<T>& a, cudaStream_t s) {
+  return detail::launch_pencil(k_normsq<T>, 0, (a.nn + kThreads - 1) / kThreads, a, s, kcPointwise);
+}
+
+template <typename T>
 cudaError_t Launch<T>::combine(const T* qk, const T* qr, double ca, double cb, double* out, long long nn,
                                cudaStream_t s) {
   const void* fn = reinterpret_cast<const void*>(k_combine<T>);

@@ -632,6 +632,31 @@ __global__ void __launch_bounds__(kThreads) k_coef(CoefArgs<T> a) {
   reduce_finish<2>(vv, a.fin);
 }
 
+// ||x + cy y||^2 (y may be null) reduced in FP64 into the Fin target: the
+// squared norm of a Crank-Nicolson right-hand side for the PCG stopping test.
+template <typename T>
+struct NormArgs {
+  const T* x;
+  const T* y;
+  double cy;
+  long long nn;
+  Fin fin;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_normsq(NormArgs<T> a) {
+  double red = 0.0;
+  const T c = T(a.cy);
+  for (long long i = (long long)blockIdx.x * kThreads + threadIdx.x; i < a.nn;
+       i += (long long)gridDim.x * kThreads) {
+    T v = a.x[i];
+    if (a.y) v += c * a.y[i];
+    red += double(v) * double(v);
+  }
+  double vv[1] = {red};
+  reduce_finish<1>(vv, a.fin);
+}
+
 // out = ca qk + cb qr in FP64 (coupling field of one tissue class)
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_combine(const T* __restrict__ qk, const T* __restrict__ qr,
