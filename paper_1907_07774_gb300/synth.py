@@ -114,13 +114,17 @@ def two_site_truth(m, value=0.5):
 def labels(c1, mask, seed, threshold=0.5, flip_fraction=0.01):
     """Threshold ``c1`` at ``threshold`` (``>=`` maps to 1) and flip a seeded
     ``flip_fraction`` of the voxels inside ``mask``."""
-    d = (np.asarray(c1) >= threshold).astype(np.float64)
-    inside = np.flatnonzero(np.asarray(mask).ravel() > 0)
+    # C order throughout: the flips index the row-major flattening, and
+    # reshape(-1) of a C-ordered array is a view, so they land in d (an input
+    # with permuted strides, e.g. a GPU FFT output, would otherwise give a
+    # copy and the flips would be lost)
+    d = np.ascontiguousarray(np.asarray(c1) >= threshold, dtype=np.float64)
+    inside = np.flatnonzero(np.ascontiguousarray(mask).reshape(-1) > 0)
     k = int(round(flip_fraction * inside.size))
     if k:
         rng = np.random.default_rng(seed)
         sel = rng.choice(inside, size=k, replace=False)
-        flat = d.ravel()
+        flat = d.reshape(-1)
         flat[sel] = 1.0 - flat[sel]
     return d
 

@@ -32,6 +32,21 @@ def test_labels_flip_exact_count_inside_mask():
     assert np.all(d[mask == 0] == 0)
 
 
+def test_labels_do_not_depend_on_the_memory_order_of_the_input():
+    # the flips index the row-major flattening; a field with permuted strides
+    # (as a GPU FFT can return) must give the same labels, flips included
+    n = (16, 12, 8)
+    mask = synth.ellipsoid_mask(n)
+    rng = np.random.default_rng(2)
+    c = rng.random(n)
+    ref = synth.labels(c, mask, 5, flip_fraction=0.05)
+    for view in (np.asfortranarray(c), np.ascontiguousarray(c.transpose(2, 0, 1)).transpose(1, 2, 0)):
+        assert not view.flags["C_CONTIGUOUS"]
+        d = synth.labels(view, mask, 5, flip_fraction=0.05)
+        assert np.array_equal(d, ref)
+    assert np.sum(ref != (c >= 0.5)) == round(0.05 * mask.sum())
+
+
 def test_lattice_centred_and_spaced():
     c = synth.lattice_centers(3, 0.5)
     assert c.shape == (27, 3)
