@@ -246,6 +246,7 @@ struct Engine : EngineBase {
   cpx<T>* twA[kNumL] = {};
   cpx<T>* twB[kNumL] = {};
   double* fac = nullptr;
+  T* fac_t = nullptr;   // the same factors in T (per-voxel sums of the basis)
   double* pdev = nullptr;
   double* gp = nullptr;
   double* phit_part = nullptr;
@@ -292,6 +293,7 @@ struct Engine : EngineBase {
       put(e ? (void**)&e->twB[i] : &dummy, sizeof(cpx<T>) * L);
     }
     put(e ? (void**)&e->fac : &dummy, sizeof(double) * size_t(np) * 3 * nmax);
+    put(e ? (void**)&e->fac_t : &dummy, sizeof(T) * size_t(np) * 3 * nmax);
     put(e ? (void**)&e->pdev : &dummy, sizeof(double) * (np + 2));
     put(e ? (void**)&e->gp : &dummy, sizeof(double) * (np + 2));
     put(e ? (void**)&e->phit_part : &dummy, sizeof(double) * size_t(np) * cfg.n[0]);
@@ -786,6 +788,7 @@ struct Engine : EngineBase {
       return cuda_fail(e, "upload p");
     PhiArgs<T> pa{};
     pa.fac = fac;
+    pa.fac_t = fac_t;
     pa.p = pdev;
     pa.out = stride ? slots[0] : f[F_C0];
     pa.np = np;
@@ -926,6 +929,7 @@ struct Engine : EngineBase {
     }
     PhiArgs<T> pa{};
     pa.fac = fac;
+    pa.fac_t = fac_t;
     pa.u = f[F_ALPHA];
     pa.part = phit_part;
     pa.np = np;
@@ -1035,6 +1039,10 @@ struct Engine : EngineBase {
         }
     cudaError_t e;
     if ((e = cudaMemcpyAsync(fac, h.data(), sizeof(double) * h.size(), cudaMemcpyHostToDevice, stream)) !=
+        cudaSuccess)
+      return cuda_fail(e, "upload basis");
+    std::vector<T> ht(h.begin(), h.end());
+    if ((e = cudaMemcpyAsync(fac_t, ht.data(), sizeof(T) * ht.size(), cudaMemcpyHostToDevice, stream)) !=
         cudaSuccess)
       return cuda_fail(e, "upload basis");
     if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_fail(e, "sync");
@@ -1308,6 +1316,7 @@ struct Engine : EngineBase {
       return cuda_fail(e, "upload v");
     PhiArgs<T> pa{};
     pa.fac = fac;
+    pa.fac_t = fac_t;
     pa.p = pdev;
     pa.out = f[F_CH];
     pa.np = np;

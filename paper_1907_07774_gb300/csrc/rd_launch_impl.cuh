@@ -285,6 +285,29 @@ template <typename T>
 cudaError_t Launch<T>::grad(int L, const GradArgs<T>& a, cudaStream_t s) {
   using namespace detail;
   const long long npairs = a.g.nn / L / 2;
+  if (a.axis != 2 && !a.q && tma_fits<T>(a.g) && aligned16(a.u0) && (!a.u1 || aligned16(a.u1)) && aligned16(a.w) &&
+      aligned16(a.kappa)) {
+    RD_DISPATCH_L(L, {
+      using TS = TmaShape<T, LL>;
+      if constexpr (TS::OK) {
+        GradTmaArgs<T> t;
+        t.has_u1 = a.u1 ? 1 : 0;
+        if (strided_map(&t.map_u0, a.u0, a.g, sizeof(T), a.axis) &&
+            strided_map(&t.map_u1, a.u1 ? a.u1 : a.u0, a.g, sizeof(T), a.axis) &&
+            strided_map(&t.map_w, a.w, a.g, sizeof(T), a.axis) &&
+            strided_map(&t.map_k, a.kappa, a.g, sizeof(T), a.axis)) {
+          t.g = a.g;
+          t.twA = a.twA;
+          t.twB = a.twB;
+          t.fin = a.fin;
+          const long long tiles = (long long)(a.g.n[2] / TS::W) * (a.axis == 1 ? a.g.n[0] : a.g.n[1]);
+          if (a.axis == 1) return launch_tma(k_grad_tma<T, LL, 1>, TS::GRAD_SMEM, TS::THREADS, tiles, t, s, kcGrad);
+          return launch_tma(k_grad_tma<T, LL, 0>, TS::GRAD_SMEM, TS::THREADS, tiles, t, s, kcGrad);
+        }
+      }
+      break;
+    })
+  }
   RD_DISPATCH_L(L, {
     constexpr size_t sm = pencil_smem<T, LL>();
     const long long blocks = (npairs + Shape<LL>::G - 1) / Shape<LL>::G;

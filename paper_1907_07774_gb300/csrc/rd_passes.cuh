@@ -516,82 +516,131 @@ struct PwArgs {
   Fin fin;
 };
 
+// The input values of one element of a pointwise step (only the ones the
+// step reads are loaded).
+template <typename T>
+struct PwVals {
+  T a, b, d, pv, rh, q;
+};
+
+template <typename T, int KIND>
+__device__ __forceinline__ PwVals<T> pw_load(long long i, const PwArgs<T>& a) {
+  constexpr bool A = KIND != kPwFwdPre && KIND != kPwState;
+  constexpr bool B = KIND == kPwFwdPost || KIND == kPwAdjPre || KIND == kPwAdjPost || KIND == kPwTlPre ||
+                     KIND == kPwTlPost;
+  constexpr bool D = KIND == kPwMisfit || KIND == kPwAdjPost || KIND == kPwTlPost;
+  constexpr bool PV = KIND == kPwFwdPre || KIND == kPwAdjPre || KIND == kPwAdjPost || KIND == kPwTlPre ||
+                      KIND == kPwState;
+  constexpr bool Q = KIND == kPwAdjPre || KIND == kPwAdjPost;
+  PwVals<T> v{T(0), T(0), T(0), T(0), T(0), T(0)};
+  if (KIND != kPwFwdPost && KIND != kPwNeg && !(KIND == kPwState && a.prev_is_state)) v.rh = a.rho1[i];
+  if (A) v.a = a.a[i];
+  if (B) v.b = a.b[i];
+  if (D) v.d = a.d[i];
+  if (PV) v.pv = a.prev[i];
+  if (Q && a.q) v.q = a.q[i];
+  return v;
+}
+
+// One element of a pointwise step from its loaded inputs: writes the
+// outputs, returns the element's term of the reduction.
+template <typename T, int KIND>
+__device__ __forceinline__ T pw_compute(long long i, const PwArgs<T>& a, const PwVals<T>& v, T s, T rho_f, T k_f,
+                                        T v_k, T v_rho) {
+  T term = T(0);
+  const T rho1 = v.rh;
+  T e = T(1);
+  if (KIND != kPwFwdPost && KIND != kPwNeg && !(KIND == kPwState && a.prev_is_state)) e = expT(rho_f * rho1 * s);
+  T cn = T(0);
+  if (KIND == kPwFwdPre || KIND == kPwAdjPre || KIND == kPwTlPre || KIND == kPwState) {
+    cn = v.pv;
+    if (!a.prev_is_state) cn = logistic(cn, e);
+  }
+  if (KIND == kPwFwdPre) {
+    a.out0[i] = logistic(cn, e);
+  } else if (KIND == kPwFwdPost) {
+    a.out0[i] = v.a + v.b;
+  } else if (KIND == kPwMisfit) {
+    const T c1 = logistic(v.a, e);
+    const T dd = v.d;
+    const T r = c1 - dd;
+    T rr = r * r, al = dd - c1;
+    if (a.md[0]) {
+      // D_m = 1/2 sum_i (m_i (1 - c) - m_D,i)^2 and its -dD_m/dc
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        const T mi = a.m[j][i];
+        const T ej = mi * (T(1) - c1) - a.md[j][i];
+        rr += ej * ej;
+        al += mi * ej;
+      }
+    }
+    term += rr;
+    a.out0[i] = al;
+    if (a.out1) a.out1[i] = c1;
+  } else if (KIND == kPwAdjPre) {
+    const T al = v.a, css = v.b;
+    const T cnext = logistic(css, e);
+    term += al * rho1 * cnext * (T(1) - cnext);
+    if (a.q) a.q[i] = v.q - s * al * cnext * (T(1) - cnext);
+    a.out0[i] = logistic_dc(css, e) * al;
+    a.out1[i] = logistic(cn, e) + css;
+    a.out2[i] = cn;
+  } else if (KIND == kPwAdjPost) {
+    const T c = v.pv;
+    const T ast = v.a + T(2) * v.b + v.d;
+    const T cs = logistic(c, e);
+    term += ast * rho1 * cs * (T(1) - cs);
+    if (a.q) a.q[i] = v.q - s * ast * cs * (T(1) - cs);
+    a.out0[i] = logistic_dc(c, e) * ast;
+  } else if (KIND == kPwTlPre) {
+    const T css = v.b;
+    const T cs = logistic(cn, e);
+    const T chs = logistic_dc(cn, e) * v.a + v_rho * s * rho1 * cs * (T(1) - cs);
+    a.out0[i] = chs;
+    a.out1[i] = T(2) * k_f * chs + v_k * (cs + css);
+  } else if (KIND == kPwTlPost) {
+    const T css = v.d;
+    const T chss = v.a + v.b;
+    const T cnext = logistic(css, e);
+    a.out0[i] = logistic_dc(css, e) * chss + v_rho * s * rho1 * cnext * (T(1) - cnext);
+  } else if (KIND == kPwNeg) {
+    T w = T(1);
+    if (a.md[0]) {
+#pragma unroll
+      for (int j = 0; j < 3; ++j) w += a.m[j][i] * a.m[j][i];
+    }
+    a.out0[i] = -w * v.a;
+  } else if (KIND == kPwState) {
+    a.out0[i] = cn;
+  }
+  return term;
+}
+
 template <typename T, int KIND>
 __global__ void __launch_bounds__(kThreads) k_pw(PwArgs<T> a) {
   const double sd = a.prm->s;
   const T s = T(sd), rho_f = T(a.prm->rho_f);
   const T k_f = T(a.prm->k_f), v_k = T(a.prm->v_k), v_rho = T(a.prm->v_rho);
   double red = 0.0;
-  for (long long i = (long long)blockIdx.x * kThreads + threadIdx.x; i < a.nn;
-       i += (long long)gridDim.x * kThreads) {
-    T rho1 = T(0), e = T(1);
-    if (KIND != kPwFwdPost && KIND != kPwNeg && !(KIND == kPwState && a.prev_is_state)) {
-      rho1 = a.rho1[i];
-      e = expT(rho_f * rho1 * s);
-    }
-    T cn = T(0);
-    if (KIND == kPwFwdPre || KIND == kPwAdjPre || KIND == kPwTlPre || KIND == kPwState) {
-      cn = a.prev[i];
-      if (!a.prev_is_state) cn = logistic(cn, e);
-    }
-    if (KIND == kPwFwdPre) {
-      a.out0[i] = logistic(cn, e);
-    } else if (KIND == kPwFwdPost) {
-      a.out0[i] = a.a[i] + a.b[i];
-    } else if (KIND == kPwMisfit) {
-      const T c1 = logistic(a.a[i], e);
-      const T dd = a.d[i];
-      const T r = c1 - dd;
-      T rr = r * r, al = dd - c1;
-      if (a.md[0]) {
-        // D_m = 1/2 sum_i (m_i (1 - c) - m_D,i)^2 and its -dD_m/dc
+  // four elements per thread and trip, a grid stride apart (every load stays
+  // coalesced): the inputs of all four are loaded before any is computed, so
+  // their loads are in flight together; the reduced terms of the four are
+  // summed in T, then added in FP64
+  const long long gs = (long long)gridDim.x * kThreads;
+  for (long long i0 = (long long)blockIdx.x * kThreads + threadIdx.x; i0 < a.nn; i0 += 4 * gs) {
+    T loc = T(0);
+    if (i0 + 3 * gs < a.nn) {
+      PwVals<T> v[4];
 #pragma unroll
-        for (int j = 0; j < 3; ++j) {
-          const T mi = a.m[j][i];
-          const T ej = mi * (T(1) - c1) - a.md[j][i];
-          rr += ej * ej;
-          al += mi * ej;
-        }
-      }
-      red += double(rr);
-      a.out0[i] = al;
-      if (a.out1) a.out1[i] = c1;
-    } else if (KIND == kPwAdjPre) {
-      const T al = a.a[i], css = a.b[i];
-      const T cnext = logistic(css, e);
-      red += double(al * rho1 * cnext * (T(1) - cnext));
-      if (a.q) a.q[i] -= s * al * cnext * (T(1) - cnext);
-      a.out0[i] = logistic_dc(css, e) * al;
-      a.out1[i] = logistic(cn, e) + css;
-      a.out2[i] = cn;
-    } else if (KIND == kPwAdjPost) {
-      const T c = a.prev[i];
-      const T ast = a.a[i] + T(2) * a.b[i] + a.d[i];
-      const T cs = logistic(c, e);
-      red += double(ast * rho1 * cs * (T(1) - cs));
-      if (a.q) a.q[i] -= s * ast * cs * (T(1) - cs);
-      a.out0[i] = logistic_dc(c, e) * ast;
-    } else if (KIND == kPwTlPre) {
-      const T css = a.b[i];
-      const T cs = logistic(cn, e);
-      const T chs = logistic_dc(cn, e) * a.a[i] + v_rho * s * rho1 * cs * (T(1) - cs);
-      a.out0[i] = chs;
-      a.out1[i] = T(2) * k_f * chs + v_k * (cs + css);
-    } else if (KIND == kPwTlPost) {
-      const T css = a.d[i];
-      const T chss = a.a[i] + a.b[i];
-      const T cnext = logistic(css, e);
-      a.out0[i] = logistic_dc(css, e) * chss + v_rho * s * rho1 * cnext * (T(1) - cnext);
-    } else if (KIND == kPwNeg) {
-      T w = T(1);
-      if (a.md[0]) {
+      for (int u = 0; u < 4; ++u) v[u] = pw_load<T, KIND>(i0 + u * gs, a);
 #pragma unroll
-        for (int j = 0; j < 3; ++j) w += a.m[j][i] * a.m[j][i];
-      }
-      a.out0[i] = -w * a.a[i];
-    } else if (KIND == kPwState) {
-      a.out0[i] = cn;
+      for (int u = 0; u < 4; ++u) loc += pw_compute<T, KIND>(i0 + u * gs, a, v[u], s, rho_f, k_f, v_k, v_rho);
+    } else {
+      for (long long i = i0; i < a.nn; i += gs)
+        loc += pw_compute<T, KIND>(i, a, pw_load<T, KIND>(i, a), s, rho_f, k_f, v_k, v_rho);
     }
+    red += double(loc);
   }
   if (a.reduce) {
     double vv[1] = {red};
@@ -647,11 +696,22 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads) k_normsq(NormArgs<T> a) {
   double red = 0.0;
   const T c = T(a.cy);
-  for (long long i = (long long)blockIdx.x * kThreads + threadIdx.x; i < a.nn;
-       i += (long long)gridDim.x * kThreads) {
-    T v = a.x[i];
-    if (a.y) v += c * a.y[i];
-    red += double(v) * double(v);
+  // as in k_pw: four elements per trip, squares summed in T, then in FP64
+  const long long gs = (long long)gridDim.x * kThreads;
+  for (long long i0 = (long long)blockIdx.x * kThreads + threadIdx.x; i0 < a.nn; i0 += 4 * gs) {
+    auto sq = [&](long long i) {
+      T v = a.x[i];
+      if (a.y) v += c * a.y[i];
+      return v * v;
+    };
+    T loc = T(0);
+    if (i0 + 3 * gs < a.nn) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) loc += sq(i0 + u * gs);
+    } else {
+      for (long long i = i0; i < a.nn; i += gs) loc += sq(i);
+    }
+    red += double(loc);
   }
   double vv[1] = {red};
   reduce_finish<1>(vv, a.fin);
@@ -680,6 +740,7 @@ __global__ void __launch_bounds__(kThreads) k_convert(const TI* __restrict__ in,
 template <typename T>
 struct PhiArgs {
   const double* fac;   // np * 3 * nmax
+  const T* fac_t;      // the same factors in T
   const double* p;     // np (device)
   T* out;              // synthesis output
   const T* u;          // projection input
@@ -694,7 +755,8 @@ struct PhiArgs {
 // order, so the result is deterministic.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_phi(PhiArgs<T> a) {
-  extern __shared__ double coef[];   // np
+  extern __shared__ double coef_raw[];   // np doubles; holds np values of T
+  T* coef = reinterpret_cast<T*>(coef_raw);
   const int n0 = a.g.n[0], n1 = a.g.n[1], n2 = a.g.n[2];
   for (long long row = blockIdx.x; row < (long long)n0 * n1; row += gridDim.x) {
     const int x0 = int(row / n1), x1 = int(row % n1);
@@ -702,19 +764,20 @@ __global__ void __launch_bounds__(kThreads) k_phi(PhiArgs<T> a) {
     for (int i = threadIdx.x; i < a.np; i += kThreads) {
       double c = a.p[i] * a.fac[(i * 3 + 0) * a.nmax + x0] * a.fac[(i * 3 + 1) * a.nmax + x1];
       if (!(fabs(c) > a.cut)) c = 0.0;
-      coef[i] = c;
+      coef[i] = T(c);
       any |= (c != 0.0);
     }
     any = __syncthreads_or(any);
+    // the field is stored in T, so the sum over the basis runs in T too
     for (int x2 = threadIdx.x; x2 < n2; x2 += kThreads) {
-      double s = 0.0;
+      T s = T(0);
       if (any) {
         for (int i = 0; i < a.np; ++i) {
-          const double c = coef[i];
-          if (c != 0.0) s += c * a.fac[(i * 3 + 2) * a.nmax + x2];
+          const T c = coef[i];
+          if (c != T(0)) s += c * a.fac_t[(i * 3 + 2) * a.nmax + x2];
         }
       }
-      a.out[row * n2 + x2] = T(s);
+      a.out[row * n2 + x2] = s;
     }
     __syncthreads();
   }
@@ -733,10 +796,11 @@ __global__ void __launch_bounds__(kThreads) k_phit(PhiArgs<T> a) {
       for (int x1 = threadIdx.x / 32; x1 < n1; x1 += kWarps) {
         const double f1 = a.fac[(i * 3 + 1) * a.nmax + x1];
         if (fabs(f0 * f1) <= a.cut) continue;
-        double r = 0.0;
+        // one lane's share of a row (n2 / 32 terms) is summed in T
+        T r = T(0);
         const T* row = a.u + ((long long)x0 * n1 + x1) * n2;
-        for (int x2 = threadIdx.x & 31; x2 < n2; x2 += 32) r += a.fac[(i * 3 + 2) * a.nmax + x2] * double(row[x2]);
-        s += f0 * f1 * r;
+        for (int x2 = threadIdx.x & 31; x2 < n2; x2 += 32) r += a.fac_t[(i * 3 + 2) * a.nmax + x2] * row[x2];
+        s += f0 * f1 * double(r);
       }
     }
     double vv = warp_sum(s);

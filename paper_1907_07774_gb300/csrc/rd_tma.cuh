@@ -129,6 +129,7 @@ struct TmaShape {
   static constexpr size_t OP_SMEM = 3 * size_t(TILE_BYTES) + XBYTES + TWBYTES + 1024;
   static constexpr size_t OPR_SMEM = 2 * size_t(TILE_BYTES) + XBYTES + TWBYTES + 1024;
   static constexpr size_t DHT_SMEM = 2 * size_t(TILE_BYTES) + XBYTES + TWBYTES + 1024;
+  static constexpr size_t GRAD_SMEM = 3 * size_t(TILE_BYTES) + XBYTES + TWBYTES + 1024;
 };
 
 // Pair (columns 2g, 2g + 1) of row `row` inside a swizzled 64-byte-row tile.
@@ -520,6 +521,130 @@ __global__ void __launch_bounds__(TmaShape<T, L>::THREADS, (MODE == kDhtSym && s
     double vv[1] = {red};
     reduce_finish<1>(vv, a.fin);
   }
+}
+
+template <typename T>
+struct GradTmaArgs {
+  CUtensorMap map_u0;
+  CUtensorMap map_u1;   // equal to map_u0 when has_u1 == 0
+  CUtensorMap map_w;
+  CUtensorMap map_k;
+  int has_u1;
+  Geom g;
+  const cpx<T>* twA;
+  const cpx<T>* twB;
+  Fin fin;
+};
+
+// Gradient pass along a strided axis (the reduction of k_grad without the
+// per-voxel output): sum_x kappa1 d_axis(u0 + u1) d_axis(w).  Three tile
+// buffers: A holds u0 and then kappa, B holds u1, C holds w.  kappa and the
+// next u1 are requested as soon as u0 + u1 is in registers, the next w once
+// w is, and the next u0 once kappa is, so every load overlaps a transform.
+template <typename T, int L, int AXIS>
+__global__ void __launch_bounds__(TmaShape<T, L>::THREADS) k_grad_tma(const __grid_constant__ GradTmaArgs<T> a) {
+  using S = TmaShape<T, L>;
+  constexpr int R = S::R, TH = S::TH, TB = S::TILE_BYTES;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  unsigned char* a_buf = smem;
+  unsigned char* b_buf = smem + TB;
+  unsigned char* c_buf = smem + 2 * TB;
+  cpx<T>* xbuf = reinterpret_cast<cpx<T>*>(smem + 3 * TB);
+  cpx<T>* tws = reinterpret_cast<cpx<T>*>(smem + 3 * TB + S::XBYTES);
+  const cpx<T>* twA = tws;
+  const cpx<T>* twB = tws + L;
+  stage_twiddles<T, L>(tws, a.twA, a.twB);
+  __shared__ uint64_t abar, bbar, cbar;
+  const int g = threadIdx.x / TH, t = threadIdx.x % TH;
+  cpx<T>* sm = xbuf + g * S::XSTRIDE;
+  const long long ntiles = (long long)(a.g.n[2] / S::W) * (AXIS == 1 ? a.g.n[0] : a.g.n[1]);
+  const T scale = T(1.0 / (double(L) * double(L)));
+  const bool two = a.has_u1 != 0;
+  TmaPending pa, pb, pc;
+  auto issue = [&](unsigned char* dst, const CUtensorMap* map, uint64_t* bar, TmaPending& pd, long long tile) {
+    int c0, c1, c2;
+    tile_coords(a.g, AXIS, S::W, tile, c0, c1, c2);
+    mbar_expect_tx(bar, TB);
+    tma_load3(dst, map, c0, c1, c2, bar);
+    ++pd.issued;
+  };
+  if (threadIdx.x == 0) {
+    mbar_init(&abar, 1);
+    mbar_init(&bbar, 1);
+    mbar_init(&cbar, 1);
+    fence_barrier_init();
+  }
+  __syncthreads();
+  const long long t0 = blockIdx.x, stride = gridDim.x;
+  if (threadIdx.x == 0 && t0 < ntiles) {
+    issue(a_buf, &a.map_u0, &abar, pa, t0);
+    if (two) issue(b_buf, &a.map_u1, &bbar, pb, t0);
+    issue(c_buf, &a.map_w, &cbar, pc, t0);
+  }
+  double red = 0.0;
+  bool bad = false;
+  int i = 0;
+  for (long long tile = t0; tile < ntiles; tile += stride, ++i) {
+    const bool more = tile + stride < ntiles;
+    // u0 is load 2i of barrier A (parity 0), kappa load 2i + 1 (parity 1)
+    bool ok = mbar_wait(&abar, 0);
+    if (two) ok = ok && mbar_wait(&bbar, i & 1);
+    if (__syncthreads_or(!ok)) { bad = true; break; }
+    ++pa.done;
+    if (two) ++pb.done;
+    cpx<T> du[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      du[r] = *tile_pair<T>(a_buf, idx_a<L>(r, t), g);
+      if (two) du[r] = du[r] + *tile_pair<T>(b_buf, idx_a<L>(r, t), g);
+    }
+    __syncthreads();   // every u0 and u1 value is in registers
+    if (threadIdx.x == 0) {
+      issue(a_buf, &a.map_k, &abar, pa, tile);
+      if (two && more) issue(b_buf, &a.map_u1, &bbar, pb, tile + stride);
+    }
+    fft_ab<T, L, -1, true>(du, sm, t, twA);
+#pragma unroll
+    for (int r = 0; r < R; ++r) du[r] = times_ik(du[r], kwave<L>(idx_b<L>(r, t)));
+    fft_ba<T, L, +1, true>(du, sm, t, twB);
+    ok = mbar_wait(&cbar, i & 1);
+    if (__syncthreads_or(!ok)) { bad = true; break; }
+    ++pc.done;
+    cpx<T> dw[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) dw[r] = *tile_pair<T>(c_buf, idx_a<L>(r, t), g);
+    __syncthreads();   // every w value is in registers
+    if (threadIdx.x == 0 && more) issue(c_buf, &a.map_w, &cbar, pc, tile + stride);
+    fft_ab<T, L, -1, true>(dw, sm, t, twA);
+#pragma unroll
+    for (int r = 0; r < R; ++r) dw[r] = times_ik(dw[r], kwave<L>(idx_b<L>(r, t)));
+    fft_ba<T, L, +1, true>(dw, sm, t, twB);
+    ok = mbar_wait(&abar, 1);
+    if (__syncthreads_or(!ok)) { bad = true; break; }
+    ++pa.done;
+    T loc = T(0);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const cpx<T> k = *tile_pair<T>(a_buf, idx_a<L>(r, t), g);
+      loc += k.x * du[r].x * dw[r].x + k.y * du[r].y * dw[r].y;
+    }
+    red += double(loc * scale);
+    __syncthreads();   // every kappa value is in registers
+    if (threadIdx.x == 0 && more) issue(a_buf, &a.map_u0, &abar, pa, tile + stride);
+  }
+  if (bad) {
+    if (threadIdx.x == 0) {
+      a.fin.st->status = kStTimeout;
+      a.fin.st->sticky = kStTimeout;
+      drain(&abar, pa);
+      drain(&bbar, pb);
+      drain(&cbar, pc);
+    }
+    return;
+  }
+  double vv[1] = {red};
+  reduce_finish<1>(vv, a.fin);
 }
 
 }  // namespace rd
