@@ -120,6 +120,29 @@ template <typename T>
 cudaError_t Launch<T>::op(int L, const OpArgs<T>& a, cudaStream_t s) {
   using namespace detail;
   const long long npairs = a.g.nn / L / 2;
+  if (a.axis == 2 && a.a_self == 0 && !a.acc_in && !a.reduce && a.out && a.fin.st && aligned16(a.u) &&
+      aligned16(a.kappa) && aligned16(a.out)) {
+    RD_DISPATCH_L(L, {
+      using TS = TmaRowShape<T, LL>;
+      if constexpr (TS::OK) {
+        const long long rows = a.g.nn / LL;
+        OpRowTmaArgs<T> t;
+        if (rows % TS::ROWS == 0 && row_map(&t.map_u, a.u, a.g, sizeof(T), TS::ROWS) &&
+            row_map(&t.map_k, a.kappa, a.g, sizeof(T), TS::ROWS)) {
+          t.out = a.out;
+          t.c0 = a.c0;
+          t.use_kf = a.use_kf;
+          t.g = a.g;
+          t.twA = a.twA;
+          t.twB = a.twB;
+          t.prm = a.prm;
+          t.st = a.fin.st;
+          return launch_tma(k_op_row_tma<T, LL>, TS::OPROW_SMEM, TS::THREADS, rows / TS::ROWS, t, s, kcOpContig);
+        }
+      }
+      break;
+    })
+  }
   if (a.axis != 2 && a.a_self == 0 && a.acc_in == a.out && a.out && tma_fits<T>(a.g) && aligned16(a.u) &&
       aligned16(a.kappa) && aligned16(a.out)) {
     RD_DISPATCH_L(L, {

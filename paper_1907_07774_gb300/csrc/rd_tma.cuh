@@ -669,6 +669,7 @@ struct TmaRowShape {
   static constexpr bool OK = (THREADS >= 32) && (THREADS % 32 == 0);
   static constexpr int TWBYTES = 2 * L * int(sizeof(cpx<T>));
   static constexpr size_t OPX_SMEM = 3 * size_t(TILE_BYTES) + XBYTES + TWBYTES + 128;
+  static constexpr size_t OPROW_SMEM = 2 * size_t(TILE_BYTES) + XBYTES + TWBYTES + 128;
   static constexpr size_t UPD_SMEM = 8 * size_t(TILE_BYTES) + XBYTES + TWBYTES + 1024;
   static constexpr size_t SETUP_SMEM = 2 * size_t(TILE_BYTES) + XBYTES + TWBYTES + 1024;
 };
@@ -691,6 +692,112 @@ __device__ __forceinline__ void tma_store2(const CUtensorMap* map, const void* s
                    reinterpret_cast<uint64_t>(map)),
                "r"(smem_addr(src)), "r"(c0), "r"(c1)
                : "memory");
+}
+
+template <typename T>
+struct OpRowTmaArgs {
+  CUtensorMap map_u;
+  CUtensorMap map_k;
+  T* out;
+  double c0;
+  int use_kf;
+  Geom g;
+  const cpx<T>* twA;
+  const cpx<T>* twB;
+  Params* prm;
+  PcgState* st;   // timeout flag
+};
+
+// out = c0 (k_f) s d_2(kappa d_2 u): the contiguous-axis pass that starts an
+// operator application (nothing accumulated, nothing reduced).  u and kappa
+// arrive as TMA row tiles, each requested for the next tile as soon as its
+// values are in registers; out leaves from registers in layout A, where the
+// TH lanes of a group hold TH consecutive elements of a row (coalesced).
+template <typename T, int L>
+__global__ void __launch_bounds__(TmaRowShape<T, L>::THREADS) k_op_row_tma(const __grid_constant__ OpRowTmaArgs<T> a) {
+  using S = TmaRowShape<T, L>;
+  constexpr int R = S::R, TH = S::TH, TB = S::TILE_BYTES;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+  unsigned char* u_buf = smem;
+  unsigned char* k_buf = smem + TB;
+  cpx<T>* xbuf = reinterpret_cast<cpx<T>*>(smem + 2 * TB);
+  cpx<T>* tws = reinterpret_cast<cpx<T>*>(smem + 2 * TB + S::XBYTES);
+  const cpx<T>* twA = tws;
+  const cpx<T>* twB = tws + L;
+  stage_twiddles<T, L>(tws, a.twA, a.twB);
+  __shared__ uint64_t ubar, kbar;
+  const int g = threadIdx.x / TH, t = threadIdx.x % TH;
+  cpx<T>* sm = xbuf + g * S::XSTRIDE;
+  const long long ntiles = a.g.nn / L / S::ROWS;
+  const T coef = T(a.c0 * (a.use_kf ? a.prm->k_f : 1.0) * a.prm->s / (double(L) * double(L)));
+  TmaPending pu, pk;
+  auto issue = [&](unsigned char* dst, const CUtensorMap* map, uint64_t* bar, TmaPending& pd, long long tile) {
+    mbar_expect_tx(bar, TB);
+    tma_load2(dst, map, 0, int(tile * S::ROWS), bar);
+    ++pd.issued;
+  };
+  if (threadIdx.x == 0) {
+    mbar_init(&ubar, 1);
+    mbar_init(&kbar, 1);
+    fence_barrier_init();
+  }
+  __syncthreads();
+  const long long t0 = blockIdx.x, stride = gridDim.x;
+  if (threadIdx.x == 0 && t0 < ntiles) {
+    issue(u_buf, &a.map_u, &ubar, pu, t0);
+    issue(k_buf, &a.map_k, &kbar, pk, t0);
+  }
+  bool bad = false;
+  int i = 0;
+  const int ra = 2 * g, rb = 2 * g + 1;
+  for (long long tile = t0; tile < ntiles; tile += stride, ++i) {
+    const bool more = tile + stride < ntiles;
+    T* orow_a = a.out + (tile * S::ROWS + ra) * L;
+    T* orow_b = a.out + (tile * S::ROWS + rb) * L;
+    bool ok = mbar_wait(&ubar, i & 1);
+    if (__syncthreads_or(!ok)) { bad = true; break; }
+    ++pu.done;
+    cpx<T> v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int n = idx_a<L>(r, t);
+      v[r] = {*row_elem<T, L>(u_buf, ra, n), *row_elem<T, L>(u_buf, rb, n)};
+    }
+    __syncthreads();   // every u value is in registers
+    if (threadIdx.x == 0 && more) issue(u_buf, &a.map_u, &ubar, pu, tile + stride);
+    fft_ab<T, L, -1, true>(v, sm, t, twA);
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = times_ik(v[r], kwave<L>(idx_b<L>(r, t)));
+    fft_ba<T, L, +1, true>(v, sm, t, twB);
+    ok = mbar_wait(&kbar, i & 1);
+    if (__syncthreads_or(!ok)) { bad = true; break; }
+    ++pk.done;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int n = idx_a<L>(r, t);
+      v[r].x *= *row_elem<T, L>(k_buf, ra, n);
+      v[r].y *= *row_elem<T, L>(k_buf, rb, n);
+    }
+    __syncthreads();   // every kappa value is in registers
+    if (threadIdx.x == 0 && more) issue(k_buf, &a.map_k, &kbar, pk, tile + stride);
+    fft_ab<T, L, -1, true>(v, sm, t, twA);
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = times_ik(v[r], kwave<L>(idx_b<L>(r, t)));
+    fft_ba<T, L, +1, true>(v, sm, t, twB);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int n = idx_a<L>(r, t);
+      orow_a[n] = coef * v[r].x;
+      orow_b[n] = coef * v[r].y;
+    }
+  }
+  if (bad && threadIdx.x == 0) {
+    a.st->status = kStTimeout;
+    a.st->sticky = kStTimeout;
+    drain(&ubar, pu);
+    drain(&kbar, pk);
+  }
 }
 
 template <typename T>
