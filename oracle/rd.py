@@ -27,7 +27,7 @@ It computes, plainly and slowly, in FP64:
 * the Picard coupling field ``q(x)`` handed to the registration step
   (Sec. 2.2).
 
-Readings where the paper is silent (each also listed in the design doc):
+Readings where the paper is silent:
 
 * Strang order ``L(tau/2) CN(tau) L(tau/2)`` with ``L_t`` the exact logistic
   flow ``c e^{rho t} / (1 - c + c e^{rho t})``.

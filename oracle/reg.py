@@ -24,8 +24,7 @@ Sec. 3.2 and 3.3):
 * the spectral preconditioner ``(beta_v (-Lap))^-1`` (zero mode ``1 /
   beta_v``).
 
-Readings where the paper defers to its references (also listed in
-DESIGN.md):
+Readings where the paper defers to its references:
 
 * ``div v = w`` is taken with ``w = 0`` (incompressible velocity), so K is
   the Leray projection ``K u = u - grad Lap^-1 div u`` onto divergence-free
