@@ -37,6 +37,7 @@ sys.path.insert(0, ROOT)
 METRIC = "fwd+adjoint gradient cell-updates/s at 256^3 (FP32-mixed vs FP64, same GB300), %HBM peak"
 UNIT = "cell-updates/s"
 FALLBACK_HBM_GBS = 6800.0
+NOMINAL_HBM_GBS = 7900.0   # GB300 HBM3e data-sheet bandwidth (context only)
 # PCG work of one FP64 gradient of this workload (rtol 1e-10), measured on
 # the GPU FP64 path; used to scale the CPU oracle sample in the reference arm.
 FP64_WORK = {"iters": 1322, "solves": 64}
@@ -296,6 +297,7 @@ def run_ours(args, rank, world, local):
     tot_ms = sum(prof[k][0] for k in pcg_classes)
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": peak_kind,
+                "frac_of_nominal": achieved / NOMINAL_HBM_GBS, "nominal_gbs": NOMINAL_HBM_GBS,
                 "traffic": ncu_traffic(dom, n), "alg_bytes_per_launch": alg_bytes,
                 "avg_launch_us": 1e3 * dms / dcount, "launches_per_step": dcount,
                 "share_of_step": dms / (ms / args.steps),
