@@ -88,6 +88,28 @@ def test_operator_and_preconditioner_match_oracle(prec, n):
     assert rel(z, want) <= TOL[prec]
 
 
+def test_operator_and_preconditioner_at_256_match_oracle():
+    """The benchmark grid (256^3, its tissue maps and k_f): one operator
+    application and one preconditioner application through the kernels the
+    benchmark runs (TMA row and strided passes at L = 256), in both
+    precisions, against the oracle on a field with smooth and rough parts."""
+    prob = synth.calibration_problem(n=256, nt=32, m=5)
+    M = orc.model_from_problem(prob, kind="numpy")
+    rng = np.random.default_rng(11)
+    u = M.phi(prob.p) + 0.1 * rng.standard_normal(prob.n)
+    want_a = M.A(u, prob.k_f)
+    want_z = M.sp.precond(u, M.s * prob.k_f * orc.kbar_positive(M.kappa1))
+    for prec in ("fp64", "mixed"):
+        ctx = gpu_for(prob, prec)
+        out = np.zeros(prob.n)
+        ctx.rd_apply_operator(prob.k_f, u, out)
+        assert rel(out, want_a) <= TOL[prec] * (10 if prec == "fp64" else 1), prec
+        z = np.zeros(prob.n)
+        ctx.rd_apply_precond(prob.k_f, u, z)
+        assert rel(z, want_z) <= TOL[prec], prec
+        del ctx
+
+
 # ---------------------------------------------------------------- solves
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 @pytest.mark.parametrize("n,nt", [((16, 16, 16), 4), ((8, 16, 32), 3), ((8, 8, 8), 2), ((32, 96, 16), 3)])
