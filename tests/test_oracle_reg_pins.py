@@ -8,7 +8,6 @@ check convergence under refinement rather than a fixed tight tolerance."""
 import math
 
 import numpy as np
-import pytest
 
 from oracle import reg as G
 from paper_1907_07774_gb300 import synth

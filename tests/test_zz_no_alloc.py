@@ -10,7 +10,6 @@ both results.  This file is collected last on purpose."""
 
 import math
 
-import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
