@@ -14,7 +14,10 @@ so the working set (> 2 GiB) is far larger than L2.
 
 ``--impl reference`` times the FP64 CPU oracle on the host instead (a
 bounded sample: one operator application and one preconditioner
-application at the same grid, scaled by the PCG work of the gradient).
+application at the same grid, scaled by the oracle's own PCG work for this
+gradient, which a full oracle run stored under tests/golden/; labelled
+"extrapolated").  The CPU baseline of the main line adds complete oracle
+gradients at 64^3 timed on one core and on all host cores.
 Multi-GPU runs (torchrun) execute independent replicas, one per rank.
 """
 
@@ -38,9 +41,7 @@ METRIC = "fwd+adjoint gradient cell-updates/s at 256^3 (FP32-mixed vs FP64, same
 UNIT = "cell-updates/s"
 FALLBACK_HBM_GBS = 6800.0
 NOMINAL_HBM_GBS = 7900.0   # GB300 HBM3e data-sheet bandwidth (context only)
-# PCG work of one FP64 gradient of this workload (rtol 1e-10), measured on
-# the GPU FP64 path; used to scale the CPU oracle sample in the reference arm.
-FP64_WORK = {"iters": 1322, "solves": 64}
+GOLDEN = os.path.join(ROOT, "tests", "golden")
 
 
 def env_rank():
@@ -168,12 +169,56 @@ class Clocks:
                 if any(r[3].replace(".", "").isdigit() for r in rows) else None}
 
 
-# algorithmic fields moved per launch of each kernel class
+# algorithmic fields moved per launch of each kernel class, over the whole grid
 FIELDS_PER_LAUNCH = {"op_axis01": 4, "op_axis2": 3, "pcg_opx": 5, "dht_plain": 2, "dht_sym": 2,
                      "dht_setup": 2, "dht_update": 7, "grad": 4}
 
 
-def cpu_oracle_sample(n, nt, k_f, seconds_budget=30.0):
+def fields_per_launch(active):
+    """Fields each class must move per launch once the tiles where kappa
+    vanishes are skipped (rd_active_tiles): the strided operator passes move
+    u, kappa, q in and q out only on active tiles (axes 0 and 1 alternate);
+    the direction kernel reads kappa only on active row tiles; the k_f
+    gradient passes (axes 2, 1, 0) skip inactive strided tiles."""
+    f0 = active["axis0"][0] / max(1, active["axis0"][1])
+    f1 = active["axis1"][0] / max(1, active["axis1"][1])
+    fr = active["rows"][0] / max(1, active["rows"][1])
+    out = dict(FIELDS_PER_LAUNCH)
+    out["op_axis01"] = 4 * 0.5 * (f0 + f1)
+    out["pcg_opx"] = 4 + fr
+    out["grad"] = 4 * (1 + f0 + f1) / 3
+    return out, {"axis0": f0, "axis1": f1, "rows": fr}
+
+
+def oracle_case(n, nt):
+    """The stored FP64 oracle run of this workload (tests/golden/, written by
+    make_golden_full.py from the oracle alone): its scalars and its labels,
+    or None."""
+    import numpy as np
+    js = os.path.join(GOLDEN, f"oracle_full_grad{n}_nt{nt}.json")
+    nz = os.path.join(GOLDEN, f"oracle_full_grad{n}_nt{nt}.npz")
+    if not (os.path.exists(js) and os.path.exists(nz)):
+        return None
+    want = json.load(open(js))
+    bits = np.load(nz)["labels_bits"]
+    labels = np.unpackbits(bits)[: n ** 3].reshape(n, n, n).astype(np.float64)
+    return want, labels
+
+
+def oracle_work(n, nt):
+    """The oracle's own PCG work for the benchmark gradient (iterations,
+    solves), stored by a full oracle run (tests/golden/make_golden_full.py,
+    PCG rtol 1e-6 as in the benchmark), or None when no run is stored."""
+    path = os.path.join(GOLDEN, f"oracle_full_work{n}_nt{nt}_rtol1e-6.json")
+    if not os.path.exists(path):
+        return None
+    d = json.load(open(path))
+    its = d["pcg_iters_forward"] + d["pcg_iters_adjoint"]
+    return {"iters": int(sum(its)), "solves": len(its), "source": os.path.relpath(path, ROOT),
+            "seconds_x86": d.get("seconds_gradient")}
+
+
+def cpu_oracle_sample(n, nt, k_f):
     """Time one FP64 oracle operator application and one preconditioner
     application on the host at grid n (the work of one PCG iteration)."""
     import numpy as np
@@ -184,7 +229,7 @@ def cpu_oracle_sample(n, nt, k_f, seconds_budget=30.0):
     t0 = time.perf_counter()
     M.A(u, k_f)
     t1 = time.perf_counter()
-    M.sp.precond(u, M.s * k_f * float(np.mean(M.kappa1)))
+    M.sp.precond(u, M.s * k_f * orc.kbar_positive(M.kappa1))
     t2 = time.perf_counter()
     return t1 - t0, t2 - t1
 
@@ -197,28 +242,131 @@ def cpu_cells_per_s(n, nt, t_apply, t_prec, iters, solves):
     return n ** 3 * nt / t, t
 
 
+def fft_flops_per_gradient(n, nt, iters, solves):
+    """Estimated floating-point operations of one gradient on the GPU path:
+    every pencil transform of length L costs 5 L log2 L flops per packed pair
+    of real pencils, i.e. 2.5 log2 L per real value; a PCG iteration makes 18
+    transforms per cell (Hartley passes 1 + 2 + 1 + 1, direction kernel 5, two
+    operator passes 4 each), a solve's set-up and right-hand side 13, an
+    adjoint step's k_f integrand 12.  Pointwise work is left out (a few per
+    cent)."""
+    per_transform = 2.5 * math.log2(n)
+    transforms = iters * 18 + solves * 13 + nt * 12
+    return transforms * per_transform * n ** 3
+
+
+def cpu_model():
+    """CPU model name of this host (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+_FULL = {"n": 64, "nt": 16, "m": 4}
+
+
+def _full_gradient_worker(args):
+    """One complete oracle gradient (single-threaded child process)."""
+    n, nt, m, d = args
+    from oracle import rd as orc
+    from paper_1907_07774_gb300 import synth
+    prob = synth.calibration_problem(n=n, nt=nt, m=m)
+    M = orc.model_from_problem(prob, rtol=1e-6, maxit=5000, kind="numpy")
+    t0 = time.perf_counter()
+    M.gradient(prob.p, prob.k_f, prob.rho_f, d)
+    return time.perf_counter() - t0, int(sum(M.iters))
+
+
+def cpu_full_gradients():
+    """Complete oracle gradients of the calibration recipe at 64^3, nt = 16
+    (PCG rtol 1e-6), timed on one core and on every host core at once (one
+    single-threaded process per core, independent problems), in
+    cell-updates/s; the data are made once by the oracle and not timed."""
+    import multiprocessing as mp
+    from oracle import rd as orc
+    from paper_1907_07774_gb300 import synth
+    n, nt, m = _FULL["n"], _FULL["nt"], _FULL["m"]
+    prob = synth.calibration_problem(n=n, nt=nt, m=m)
+    M = orc.model_from_problem(prob, rtol=1e-6, maxit=5000, kind="numpy")
+    c_true, _ = M.forward(prob.p_true, prob.k_f_true, prob.rho_f_true)
+    d = synth.labels(c_true, synth.ellipsoid_mask(prob.n), prob.seed + 7)
+    cores = os.cpu_count() or 1
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = "1"
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(1) as pool:
+        t1, its = pool.map(_full_gradient_worker, [(n, nt, m, d)])[0]
+    t0 = time.perf_counter()
+    with ctx.Pool(cores) as pool:
+        res = pool.map(_full_gradient_worker, [(n, nt, m, d)] * cores)
+    tall = time.perf_counter() - t0
+    cells = n ** 3 * nt
+    return {"workload": f"oracle gradient {n}^3 nt={nt} np={m ** 3} pcg_rtol=1e-6 (numpy FFT, FP64)",
+            "pcg_iters": its, "one_core": {"seconds": t1, "value": cells / t1, "cores": 1},
+            "all_cores": {"seconds_wall": tall, "value": cores * cells / tall, "cores": cores,
+                          "note": "one single-threaded oracle gradient per core, run at once; wall time "
+                                  "includes process start-up"},
+            "unit": UNIT}
+
+
+def cpu_extrapolated(n, nt, k_f):
+    """The oracle on the benchmark workload itself: one operator and one
+    preconditioner application timed at n^3, scaled by the oracle's own PCG
+    work for the whole gradient."""
+    ta, tp = cpu_oracle_sample(n, nt, k_f)
+    w = oracle_work(n, nt)
+    if w is None:
+        return None, ta, tp
+    v, tgrad = cpu_cells_per_s(n, nt, ta, tp, w["iters"], w["solves"])
+    return {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"extrapolated: one FP64 operator application ({ta:.2f} s) and one preconditioner "
+                      f"application ({tp:.2f} s) of the oracle (numpy FFT) at {n}^3, scaled by the oracle's own "
+                      f"PCG work for this gradient ({w['iters']} iterations in {w['solves']} solves at rtol 1e-6, "
+                      f"from {w['source']}): {tgrad:.0f} s per gradient",
+            "seconds_per_gradient": tgrad}, ta, tp
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
     n, nt = args.n, args.nt
-    vals = []
-    last = None
+    w = oracle_work(n, nt)
+    if w is None:
+        print(json.dumps({"impl": "reference", "unavailable": f"no stored oracle PCG work for {n}^3 nt={nt}"}))
+        return 0
+    steps = []
     for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
         ta, tp = cpu_oracle_sample(n, nt, 0.02)
-        v, tgrad = cpu_cells_per_s(n, nt, ta, tp, FP64_WORK["iters"], FP64_WORK["solves"])
+        dt = time.perf_counter() - t0
         if i >= args.warmup:
-            vals.append(v)
-            last = (ta, tp, tgrad)
-    value = statistics.median(vals)
-    sample = (f"oracle (numpy FFT, FP64) one operator application ({last[0]:.2f} s) and one "
-              f"preconditioner application ({last[1]:.2f} s) at {n}^3, scaled by the PCG work of "
-              f"the FP64 gradient ({FP64_WORK['iters']} iterations, {FP64_WORK['solves']} solves, nt={nt}): "
-              f"{last[2]:.0f} s per gradient")
+            steps.append((dt, ta, tp))
+    ta = statistics.median(s[1] for s in steps)
+    tp = statistics.median(s[2] for s in steps)
+    value, tgrad = cpu_cells_per_s(n, nt, ta, tp, w["iters"], w["solves"])
+    ms_step = 1e3 * statistics.mean(s[0] for s in steps)
+    sample = (f"extrapolated: each step times one FP64 operator application ({ta:.2f} s) and one preconditioner "
+              f"application ({tp:.2f} s) of the oracle (numpy FFT) at {n}^3 on one core; value = the gradient's "
+              f"cell-updates over the oracle's own PCG work for it ({w['iters']} iterations in {w['solves']} "
+              f"solves at rtol 1e-6, {w['source']}): {tgrad:.0f} s per gradient")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * n ** 3 * nt / value,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": f"rd_gradient {n}^3 nt={nt} np=125 fp64 oracle"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "data": "synthetic", "config": {"workload": f"rd_gradient {n}^3 nt={nt} np=125 fp64 oracle, "
+                                                        f"per-iteration sample"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                             "nproc": os.cpu_count(), "cpu_model": cpu_model()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -241,9 +389,17 @@ def run_ours(args, rank, world, local):
     n, nt = args.n, args.nt
     prob = problem(n, nt)
     ctx = R.context_for(prob, prec="mixed", pcg_rtol=1e-6, pcg_maxit=500, ckpt_stride=args.ckpt_stride)
-    c_true = torch.zeros(prob.n, dtype=torch.float64, device="cuda")
-    ctx.rd_forward(prob.p_true, prob.k_f_true, prob.rho_f_true, c_true)
-    d_host = synth.labels(c_true.cpu().numpy(), synth.ellipsoid_mask(prob.n), prob.seed + 7)
+    gold = oracle_case(n, nt)
+    if gold is not None:
+        # the labels of the stored oracle run (thresholded oracle c_true(1))
+        d_host = gold[1]
+        data_src = "labels of the stored FP64 oracle run (tests/golden)"
+    else:
+        c_true = torch.zeros(prob.n, dtype=torch.float64, device="cuda")
+        ctx.rd_forward(prob.p_true, prob.k_f_true, prob.rho_f_true, c_true)
+        d_host = synth.labels(c_true.cpu().numpy(), synth.ellipsoid_mask(prob.n), prob.seed + 7)
+        del c_true
+        data_src = "labels of the GPU mixed c_true(1)"
     d_dev = torch.from_numpy(d_host).cuda()
     m_dev = [torch.from_numpy(x).cuda() for x in (prob.m_wm, prob.m_gm, prob.m_csf)]
     ctx.rd_set_tissue(*m_dev)
@@ -287,13 +443,14 @@ def run_ours(args, rank, world, local):
 
     # ---- roofline of the dominant kernel class
     esz = 4
-    dom = max((k for k in prof if k in FIELDS_PER_LAUNCH), key=lambda k: prof[k][0])
+    fpl, act_frac = fields_per_launch(ctx.rd_active_tiles())
+    dom = max((k for k in prof if k in fpl), key=lambda k: prof[k][0])
     dms, dcount = prof[dom]
-    alg_bytes = FIELDS_PER_LAUNCH[dom] * n ** 3 * esz
+    alg_bytes = fpl[dom] * n ** 3 * esz
     achieved = alg_bytes / (dms / dcount / 1e3) / 1e9
     peak, peak_kind = measured_peaks()
-    pcg_classes = [k for k in FIELDS_PER_LAUNCH if k in prof and prof[k][1]]
-    tot_bytes = sum(FIELDS_PER_LAUNCH[k] * n ** 3 * esz * prof[k][1] for k in pcg_classes)
+    pcg_classes = [k for k in fpl if k in prof and prof[k][1]]
+    tot_bytes = sum(fpl[k] * n ** 3 * esz * prof[k][1] for k in pcg_classes)
     tot_ms = sum(prof[k][0] for k in pcg_classes)
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": peak_kind,
@@ -303,7 +460,10 @@ def run_ours(args, rank, world, local):
                 "share_of_step": dms / (ms / args.steps),
                 "fft_operator_kernels_time_weighted_gbs": tot_bytes / (tot_ms / 1e3) / 1e9,
                 "fft_operator_kernels_frac": tot_bytes / (tot_ms / 1e3) / 1e9 / peak,
-                "timing": "per-launch CUDA events in one profiled step after the timed region"}
+                "timing": "per-launch CUDA events in one profiled step after the timed region (host-driven "
+                          "PCG loop: its class times sum to a little more than the graph-run step)",
+                "active_tile_fraction": act_frac,
+                "alg_fields_per_launch": {k: fpl[k] for k in pcg_classes}}
     per_class = {k: {"ms_per_step": v[0], "launches_per_step": v[1]} for k, v in prof.items() if v[1]}
 
     # ---- end to end through the C ABI from pinned host buffers
@@ -323,6 +483,31 @@ def run_ours(args, rank, world, local):
            "h2d_bytes_per_step": 4 * n ** 3 * 8 + len(p) * 8,
            "d2h_bytes_per_step": (len(p) + 2) * 8 + 8}
 
+    # ---- the same gradient with sqrt(nt) checkpoints (the adjoint recomputes
+    # the states of each segment), and the batched uneven workload
+    ckpt = None
+    batch = None
+    if rank == 0 and not args.no_extras:
+        s_ck = int(math.ceil(math.sqrt(nt)))
+        cck = R.context_for(prob, prec="mixed", pcg_rtol=1e-6, pcg_maxit=500, ckpt_stride=s_ck)
+        cck.rd_set_data(d_dev)
+        for _ in range(2):
+            Jc, gc = cck.rd_gradient(p, k_f, rho_f)
+        torch.cuda.synchronize()
+        e4, e5 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e4.record(stream)
+        for _ in range(3):
+            Jc, gc = cck.rd_gradient(p, k_f, rho_f)
+        e5.record(stream)
+        torch.cuda.synchronize()
+        ms_ck = e4.elapsed_time(e5) / 3
+        ckpt = {"ckpt_stride": s_ck, "value": cells / (ms_ck / 1e3), "unit": UNIT, "ms_per_step": ms_ck,
+                "steps": 3, "stored_states": (nt + s_ck - 1) // s_ck + s_ck,
+                "grad_bitwise_equal_to_store_all": bool(np.array_equal(gc, g))}
+        del cck
+        torch.cuda.empty_cache()
+        batch = batch_measure(R, synth, torch, 3, 1)
+
     # ---- FP64 path on the same GPU
     fp64 = None
     if args.fp64_steps > 0 and rank == 0:
@@ -336,8 +521,17 @@ def run_ours(args, rank, world, local):
             J64, g64 = c64.rd_gradient(p, k_f, rho_f)
         torch.cuda.synchronize()
         s64 = (time.perf_counter() - t0) / args.fp64_steps
-        fp64 = {"value": cells / s64, "ms_per_step": 1e3 * s64, "pcg_iters": c64.rd_last_pcg_iters(),
-                "pcg_solves": c64.rd_last_pcg_solves(),
+        it64, so64 = c64.rd_last_pcg_iters(), c64.rd_last_pcg_solves()
+        flops64 = fft_flops_per_gradient(n, nt, it64, so64)
+        fma64 = R.rd_probe_fma_rate("fp64")
+        fp64 = {"value": cells / s64, "ms_per_step": 1e3 * s64, "pcg_iters": it64, "pcg_solves": so64,
+                "alu_roofline": {"bound": "alu", "fma_peak_tflops_measured": fma64,
+                                 "est_tflops_achieved": flops64 / s64 / 1e12,
+                                 "frac": flops64 / s64 / 1e12 / fma64,
+                                 "est_flops_per_gradient": flops64,
+                                 "fp32_fma_peak_tflops_measured": R.rd_probe_fma_rate("mixed"),
+                                 "note": "flops estimated from the transform count (bench.fft_flops_per_gradient); "
+                                         "peak from rd_probe_fma_rate (register FMA loop)"},
                 "mixed_speedup": (cells * args.steps / (ms / 1e3)) / (cells / s64),
                 "mixed_grad_rel_err_vs_fp64": float(np.linalg.norm(g - g64) / np.linalg.norm(g64)),
                 "mixed_misfit_rel_err_vs_fp64": abs(J - J64) / abs(J64)}
@@ -346,14 +540,25 @@ def run_ours(args, rank, world, local):
     # ---- CPU oracle baseline (rank 0, N = 1 only)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        w = fp64 or {"pcg_iters": FP64_WORK["iters"], "pcg_solves": FP64_WORK["solves"]}
-        ta, tp = cpu_oracle_sample(n, nt, k_f)
-        v, tgrad = cpu_cells_per_s(n, nt, ta, tp, w["pcg_iters"], w["pcg_solves"])
-        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"one FP64 operator application ({ta:.2f} s) and one preconditioner application "
-                         f"({tp:.2f} s) of the oracle (numpy FFT) at {n}^3, scaled by the FP64 gradient's "
-                         f"PCG work ({w['pcg_iters']} iterations, {w['pcg_solves']} solves): {tgrad:.0f} s"}
+        cpu, ta, tp = cpu_extrapolated(n, nt, k_f)
+        if cpu is None:
+            cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": f"no stored oracle PCG work for {n}^3 nt={nt}; one operator application "
+                             f"{ta:.2f} s, one preconditioner application {tp:.2f} s"}
+        cpu["nproc"] = os.cpu_count()
+        cpu["cpu_model"] = cpu_model()
+        if not args.no_cpu_full:
+            cpu["measured_full_gradients"] = cpu_full_gradients()
 
+    vs_oracle = None
+    if gold is not None:
+        want = gold[0]
+        g_or = np.asarray(want["gradient"])
+        vs_oracle = {"grad_rel_l2": float(np.linalg.norm(g - g_or) / np.linalg.norm(g_or)),
+                     "misfit_rel": abs(J - want["misfit"]) / abs(want["misfit"]), "tolerance": 2e-4,
+                     "oracle_pcg_rtol": want["case"]["rtol"]}
+        if fp64 is not None:
+            vs_oracle["fp64_grad_rel_l2"] = float(np.linalg.norm(g64 - g_or) / np.linalg.norm(g_or))
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -364,8 +569,10 @@ def run_ours(args, rank, world, local):
                                                                  "working set > 2 GiB)",
                            "parallelism": "replicas" if world > 1 else "single"},
                 "misfit": J, "pcg_iters_per_step": iters, "pcg_solves_per_step": solves,
+                "data_labels": data_src, "vs_fp64_oracle": vs_oracle,
                 "gpu_launches": launches_per_step * args.steps, "clocks": clocks, "roofline": roofline, "e2e": e2e,
-                "cpu_baseline": cpu, "fp64": fp64, "kernel_classes": per_class, "autotuned_blocks": tuned}
+                "cpu_baseline": cpu, "fp64": fp64, "checkpointed": ckpt, "batch": batch,
+                "kernel_classes": per_class, "autotuned_blocks": tuned}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
@@ -389,14 +596,12 @@ def _calibrated_context(R, synth, torch, prob, prec, **kw):
     return ctx, d
 
 
-def run_batch(args, rank, world, local):
+def batch_measure(R, synth, torch, steps, warmup):
     """48 independent problems of uneven size (16 each at 64^3, 96^3, 128^3,
     nt = 16, mixed), own tissue seeds, k_f ~ U(0.01, 0.1), rho_f ~ U(5, 15),
-    all gradients in one CUDA-graph launch per step."""
+    all gradients in one CUDA-graph launch per step; the same 48 gradients
+    one after another for comparison."""
     import numpy as np
-    torch = _gpu_setup(local)
-    from paper_1907_07774_gb300 import rd as R
-    from paper_1907_07774_gb300 import synth
     rng = np.random.default_rng(3)
     ctxs, thetas, cells = [], [], 0
     for i, n in enumerate([64] * 16 + [96] * 16 + [128] * 16):
@@ -407,27 +612,36 @@ def run_batch(args, rank, world, local):
         ctxs.append(ctx)
         thetas.append((prob.p, prob.k_f, prob.rho_f))
         cells += n ** 3 * 16
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         R.rd_batch_gradient(ctxs, thetas)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(args.steps):
+    for _ in range(steps):
         Js, gs = R.rd_batch_gradient(ctxs, thetas)
     torch.cuda.synchronize()
-    dt = (time.perf_counter() - t0) / args.steps
-    # the same 48 gradients one after another, for comparison
+    dt = (time.perf_counter() - t0) / steps
     t1 = time.perf_counter()
     for c, t in zip(ctxs, thetas):
         c.rd_gradient(*t)
     torch.cuda.synchronize()
     seq = time.perf_counter() - t1
-    line = {"metric": "batched fwd+adjoint gradient cell-updates/s, 48 uneven instances", "value": cells / dt,
-            "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt,
-            "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+    del ctxs
+    torch.cuda.empty_cache()
+    return {"metric": "batched fwd+adjoint gradient cell-updates/s, 48 uneven instances", "value": cells / dt,
+            "unit": UNIT, "steps": steps, "warmup": warmup, "ms_per_step": 1e3 * dt,
             "config": {"workload": "rd_batch_gradient: 16 x 64^3, 16 x 96^3, 16 x 128^3, nt=16, mixed, "
                                    "one graph launch per step"},
             "sequential_ms": 1e3 * seq, "batch_speedup_vs_sequential": seq / dt,
             "misfit_range": [min(Js), max(Js)]}
+
+
+def run_batch(args, rank, world, local):
+    """The batched workload alone (see batch_measure)."""
+    torch = _gpu_setup(local)
+    from paper_1907_07774_gb300 import rd as R
+    from paper_1907_07774_gb300 import synth
+    res = batch_measure(R, synth, torch, args.steps, args.warmup)
+    line = dict(res, n_gpus=1, higher_is_better=True, dtype="f32", data="synthetic")
     print(json.dumps(line), flush=True)
     return 0
 
@@ -691,6 +905,10 @@ def main():
     ap.add_argument("--ckpt-stride", type=int, default=0)
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the checkpointed gradient and the batched workload of the main line")
+    ap.add_argument("--no-cpu-full", action="store_true",
+                    help="skip the complete 64^3 oracle gradients of the CPU baseline")
     ap.add_argument("--workload", default="gradient",
                     choices=["gradient", "batch", "newton", "gn", "picard", "tumor_inv", "registration",
                              "picard_loop"],

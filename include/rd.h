@@ -35,7 +35,12 @@
  *   - Adjoint convention: alpha(1) = d - c(1) (Eq. tumor:adj-final).
  *   - Errors are returned as status codes; a call never aborts the process.
  *     rd_last_error() gives a message.  RD_ERR_NOCONV means some PCG solve
- *     hit pcg_maxit; results are still written.
+ *     hit pcg_maxit; results are still written.  RD_ERR_NONFINITE means a
+ *     NaN or Inf reached a solver reduction (from the tissue maps or the
+ *     data); the context stays usable once the inputs are replaced.
+ *   - Argument checks happen before any launch (RD_ERR_ARG): field pointers
+ *     must be non-null and 8-byte aligned; p, v, k_f, rho_f must be finite
+ *     and k_f >= 0.
  *   - A context is not thread safe.  Calls are ordered on its stream; calls
  *     returning host values (rd_gradient, rd_hessvec, rd_forward with a
  *     misfit) synchronise that stream.
@@ -206,8 +211,12 @@ rd_status rd_apply_precond(rd_ctx* ctx, double k_f, const double* r, double* z);
  * until exit.  The first call on a device finds that array's address and
  * uploads the tables (synchronously); make that first call before any stream
  * capture.  All calls share the array, so calls that overlap on the GPU race;
- * order them on one stream.  r is not modified; z may not alias r; both
- * must be 16-byte aligned (RD_ERR_ARG otherwise). */
+ * order them on one stream.  Each call starts by clearing the array's solver
+ * state and counters on `stream`, so nothing of an earlier call is read.
+ * coef must be finite and >= 0; r is not modified; z may not alias r; both
+ * must be 16-byte aligned (RD_ERR_ARG otherwise).  The passes' device-side
+ * waits are bounded; if one gives up, z is left incomplete and this entry
+ * point, having no status buffer of the caller's, cannot report it. */
 rd_status rd_apply_precond_static(const int n[3], double coef, const double* r, double* z, void* stream);
 
 /* Counters of the last call: PCG iterations summed over its solves, and
@@ -239,6 +248,34 @@ rd_status rd_autotune(rd_ctx* ctx, int reps, int* caps, int ncaps);
 void rd_autotune_clear(void);
 
 /* Message of the last failing call ("" if none). */
+/* Self-test of the bounded device-side wait that every TMA pass uses (no
+ * counterpart in the paper; it lets a test reach the timeout path without
+ * hanging anything).  One block arms an mbarrier for a 16-byte transaction
+ * and, if copy != 0, issues a 16-byte bulk copy from src16 (device, 16-byte
+ * aligned) that completes it; it then waits with at most `polls` polls
+ * (1 .. the passes' own limit, 2^26) and writes to *status (device int,
+ * 4-byte aligned): 0 when the wait completed and the copied bytes match, 7
+ * (the timeout code that the passes record, reported as RD_ERR_CUDA "a TMA
+ * wait timed out") when it gave up, -1 when the copied bytes differ.
+ * Asynchronous on `stream`; RD_ERR_ARG for bad arguments. */
+rd_status rd_selftest_bounded_wait(unsigned polls, int copy, const void* src16, int* status, void* stream);
+
+/* Work actually done by the operator passes: after rd_set_tissue, counts[0..5]
+ * = (active, all) tiles of the axis-0 strided passes, the axis-1 strided
+ * passes and the contiguous-axis row tiles.  A tile is active when kappa1 is
+ * not identically zero on it; the operator d_a(kappa d_a u) and the k_f
+ * integrand vanish exactly on the others (kappa = 0 outside the brain,
+ * Sec. 2.1), so the passes skip them.  RD_ERR_STATE before rd_set_tissue. */
+rd_status rd_active_tiles(const rd_ctx* ctx, long long* counts);
+
+/* Hardware probe (no counterpart in the paper): the fused multiply-add rate
+ * of the current device in TFLOP/s (2 flops per FMA), FP64 for RD_FP64 and
+ * FP32 for RD_MIXED, from a register-only FMA loop over every SM timed with
+ * CUDA events.  It places the FP64 path, whose FFT passes do ~2-6 flops per
+ * byte, on the arithmetic roofline.  Allocates and frees a small output
+ * buffer; synchronous. */
+rd_status rd_probe_fma_rate(int prec, double* tflops);
+
 const char* rd_last_error(const rd_ctx* ctx);
 
 /* Release the context (and the workspace if the library allocated it). */

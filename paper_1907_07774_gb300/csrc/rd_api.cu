@@ -198,6 +198,45 @@ constexpr int kCouplingFields = 2;  // per-voxel k_f and rho_f integrands of the
 
 }  // namespace
 
+// Tiles of the TMA passes on which kappa1 is not identically zero.  The
+// operator d_a(kappa d_a u) and the k_f integrand kappa grad(a).grad(w)
+// vanish exactly on the others (the brain sits inside the periodic box with
+// kappa = 0 outside, Sec. 2.1 and 3.3), so those passes skip them.
+//   f0: strided tiles of axis 0, index i1 * nb + i2 / W
+//   f1: strided tiles of axis 1, index i0 * nb + i2 / W
+//   fr: row tiles of the contiguous axis, index (i0 n1 + i1) / rows
+template <typename T>
+__global__ void k_kappa_tiles(const T* __restrict__ kappa, Geom g, int W, int rows, int* f0, int* f1, int* fr) {
+  const int n1 = g.n[1], n2 = g.n[2];
+  const int nb = n2 / W;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < g.nn;
+       i += (long long)gridDim.x * blockDim.x) {
+    if (kappa[i] == T(0)) continue;
+    const int i2 = int(i % n2);
+    const long long row = i / n2;
+    const int i1 = int(row % n1), i0 = int(row / n1);
+    if (nb > 0) {
+      f0[i1 * nb + i2 / W] = 1;
+      f1[i0 * nb + i2 / W] = 1;
+    }
+    fr[row / rows] = 1;
+  }
+}
+
+// Rows per tile of the contiguous-axis TMA kernels for pencil length L.
+template <typename T>
+int row_tile_rows(int L) {
+  switch (L) {
+    case 8: return TmaRowShape<T, 8>::ROWS;
+    case 16: return TmaRowShape<T, 16>::ROWS;
+    case 32: return TmaRowShape<T, 32>::ROWS;
+    case 64: return TmaRowShape<T, 64>::ROWS;
+    case 96: return TmaRowShape<T, 96>::ROWS;
+    case 128: return TmaRowShape<T, 128>::ROWS;
+    default: return TmaRowShape<T, 256>::ROWS;
+  }
+}
+
 struct EngineBase {
   virtual ~EngineBase() {}
   rd_config cfg{};
@@ -213,6 +252,10 @@ struct EngineBase {
   double theta_kf = 0, theta_rho = 0;
   std::vector<double> theta_p, last_grad;
   bool nonconv = false;
+  // tiles of the TMA passes where kappa1 is not identically zero (strided
+  // axis 0, strided axis 1, contiguous-axis row tiles), and all tiles
+  long long active_tiles[3] = {0, 0, 0};
+  long long all_tiles[3] = {0, 0, 0};
 
   virtual rd_status set_tissue(const double*, const double*, const double*) = 0;
   virtual rd_status set_basis(const double*, double) = 0;
@@ -273,6 +316,12 @@ struct Engine : EngineBase {
   double* hp = nullptr;                 // pinned host copy of p (or v)
   double* hgp = nullptr;                // pinned host copy of g_p
   double* hv = nullptr;                 // pinned host copy of a direction v
+  // tiles where kappa1 is not identically zero (see k_kappa_tiles): lists of
+  // the strided tiles of axes 0 and 1, a flag per row tile, and the two list
+  // lengths (device)
+  int* tl[2] = {};
+  int* rowact = nullptr;
+  int* tcount = nullptr;
 
   // ------------------------------------------------------------ set-up
   static size_t layout(Carve& c, const rd_config& cfg, int np, Engine* e) {
@@ -297,6 +346,14 @@ struct Engine : EngineBase {
     put(e ? (void**)&e->pdev : &dummy, sizeof(double) * (np + 2));
     put(e ? (void**)&e->gp : &dummy, sizeof(double) * (np + 2));
     put(e ? (void**)&e->phit_part : &dummy, sizeof(double) * size_t(np) * cfg.n[0]);
+    {
+      const int W = 64 / int(sizeof(T));
+      const long long nb = (cfg.n[2] + W - 1) / W;
+      put(e ? (void**)&e->tl[0] : &dummy, sizeof(int) * size_t(cfg.n[1] * nb));
+      put(e ? (void**)&e->tl[1] : &dummy, sizeof(int) * size_t(cfg.n[0] * nb));
+      put(e ? (void**)&e->rowact : &dummy, sizeof(int) * size_t(cfg.n[0]) * cfg.n[1]);
+      put(e ? (void**)&e->tcount : &dummy, sizeof(int) * 4);
+    }
     for (int i = 0; i < 3; ++i) put(e ? (void**)&e->stage[i] : &dummy, sizeof(double) * nn);
     for (int i = 0; i < F_COUNT; ++i) put(e ? (void**)&e->f[i] : &dummy, sizeof(T) * nn);
     if (cfg.moving_atlas)
@@ -458,6 +515,10 @@ struct Engine : EngineBase {
       a.twB = twB[lidx(L)];
       a.prm = prm;
       a.fin = fin(kFinNone);
+      if (axis != 2) {
+        a.tiles = tl[axis];
+        a.ntiles_act = &tcount[axis];
+      }
       cudaError_t e = L_::op(L, a, stream);
       if (e != cudaSuccess) return e;
     }
@@ -516,6 +577,7 @@ struct Engine : EngineBase {
       a.prm = prm;
       a.st = st;
       a.fin = fin(kFinPqAdd, 0, 1.0 / (double(g.n[2]) * g.n[2]));
+      a.rowact = rowact;
       if ((e = L_::pcg_opx(g.n[2], a, stream)) != cudaSuccess) return e;
     }
     for (int axis : {1, 0}) {
@@ -534,6 +596,8 @@ struct Engine : EngineBase {
       a.twB = twB[lidx(g.n[axis])];
       a.prm = prm;
       a.fin = fin(axis == 0 ? kFinPqLast : kFinPqAdd, 0, 1.0 / (double(g.n[axis]) * g.n[axis]));
+      a.tiles = tl[axis];
+      a.ntiles_act = &tcount[axis];
       if ((e = L_::op(g.n[axis], a, stream)) != cudaSuccess) return e;
     }
     {
@@ -881,6 +945,10 @@ struct Engine : EngineBase {
       ga.twA = twA[lidx(g.n[axis])];
       ga.twB = twB[lidx(g.n[axis])];
       ga.fin = fin(kFinAcc, kAccGk, hprm->s * hprm->h3);
+      if (axis != 2) {
+        ga.tiles = tl[axis];
+        ga.ntiles_act = &tcount[axis];
+      }
       if ((e = L_::grad(g.n[axis], ga, stream)) != cudaSuccess) return cuda_fail(e, "grad pass");
     }
     PwArgs<T> b = pw_args();
@@ -987,6 +1055,57 @@ struct Engine : EngineBase {
   }
 
   // ------------------------------------------------------------ API
+  // Flags of the tiles on which kappa1 is not identically zero, compacted on
+  // the host into ascending lists (the order the passes would visit them in).
+  cudaError_t kappa_tiles() {
+    const int W = 64 / int(sizeof(T));
+    const int nb = g.n[2] / W;
+    const int rows = row_tile_rows<T>(g.n[2]);
+    all_tiles[0] = (long long)g.n[1] * nb;
+    all_tiles[1] = (long long)g.n[0] * nb;
+    all_tiles[2] = ((long long)g.n[0] * g.n[1] + rows - 1) / rows;
+    cudaError_t e;
+    for (int a = 0; a < 2; ++a)
+      if (all_tiles[a] > 0 && (e = cudaMemsetAsync(tl[a], 0, sizeof(int) * all_tiles[a], stream)) != cudaSuccess)
+        return e;
+    if ((e = cudaMemsetAsync(rowact, 0, sizeof(int) * all_tiles[2], stream)) != cudaSuccess) return e;
+    const int blocks = int(std::min<long long>((nn + 255) / 256, 4096));
+    k_kappa_tiles<T><<<blocks, 256, 0, stream>>>(f[F_KAPPA1], g, W, rows, tl[0], tl[1], rowact);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    std::vector<int> h0(all_tiles[0]), h1(all_tiles[1]);
+    if (all_tiles[0] > 0 && (e = cudaMemcpyAsync(h0.data(), tl[0], sizeof(int) * all_tiles[0],
+                                                 cudaMemcpyDeviceToHost, stream)) != cudaSuccess)
+      return e;
+    if (all_tiles[1] > 0 && (e = cudaMemcpyAsync(h1.data(), tl[1], sizeof(int) * all_tiles[1],
+                                                 cudaMemcpyDeviceToHost, stream)) != cudaSuccess)
+      return e;
+    std::vector<int> hr(all_tiles[2]);
+    if ((e = cudaMemcpyAsync(hr.data(), rowact, sizeof(int) * all_tiles[2], cudaMemcpyDeviceToHost, stream)) !=
+        cudaSuccess)
+      return e;
+    if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return e;
+    std::vector<int> l0, l1;
+    for (int t = 0; t < (int)h0.size(); ++t)
+      if (h0[t]) l0.push_back(t);
+    for (int t = 0; t < (int)h1.size(); ++t)
+      if (h1[t]) l1.push_back(t);
+    long long nr = 0;
+    for (int v : hr) nr += v ? 1 : 0;
+    active_tiles[0] = (long long)l0.size();
+    active_tiles[1] = (long long)l1.size();
+    active_tiles[2] = nr;
+    int cnt[4] = {int(l0.size()), int(l1.size()), int(nr), 0};
+    if (!l0.empty() && (e = cudaMemcpyAsync(tl[0], l0.data(), sizeof(int) * l0.size(), cudaMemcpyHostToDevice,
+                                            stream)) != cudaSuccess)
+      return e;
+    if (!l1.empty() && (e = cudaMemcpyAsync(tl[1], l1.data(), sizeof(int) * l1.size(), cudaMemcpyHostToDevice,
+                                            stream)) != cudaSuccess)
+      return e;
+    if ((e = cudaMemcpyAsync(tcount, cnt, sizeof(cnt), cudaMemcpyHostToDevice, stream)) != cudaSuccess) return e;
+    // the host vectors are pageable and local: wait until the copies are done
+    return cudaStreamSynchronize(stream);
+  }
+
   rd_status set_tissue(const double* m0, const double* m1, const double* m2) override {
     cudaError_t e;
     const double* d[3];
@@ -1008,6 +1127,7 @@ struct Engine : EngineBase {
     a.nn = nn;
     a.fin = fin(kFinRatio, 0, 1.0, &prm->kbar1);   // mean of kappa1 where it is positive
     if ((e = L_::coef(a, stream)) != cudaSuccess) return cuda_fail(e, "coefficients");
+    if ((e = kappa_tiles()) != cudaSuccess) return cuda_fail(e, "kappa tiles");
     if (cfg.moving_atlas)
       for (int j = 0; j < 3; ++j)
         if ((e = L_::from_f64(d[j], anat[j], nn, stream)) != cudaSuccess) return cuda_fail(e, "tissue maps");
@@ -1380,6 +1500,97 @@ static bool valid_shape(const rd_config* c) {
   return true;
 }
 
+namespace {
+// Self-test of the bounded mbarrier wait used by every TMA pass: one block
+// arms a barrier for 16 bytes of transaction and either issues a 16-byte bulk
+// copy that completes it (copy = 1) or issues nothing (copy = 0), then waits
+// with `polls` polls.  The outcome (kStOk or kStTimeout) goes to *status.
+__global__ void k_selftest_wait(const int4* src, unsigned polls, int copy, int* status) {
+  __shared__ alignas(16) int4 buf;
+  __shared__ alignas(8) uint64_t bar;
+  if (threadIdx.x != 0) return;
+  rd::mbar_init(&bar, 1);
+  rd::fence_barrier_init();
+  rd::mbar_expect_tx(&bar, 16);
+  if (copy)
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], 16, [%2];" ::"r"(
+            rd::smem_addr(&buf)),
+        "l"(reinterpret_cast<uint64_t>(src)), "r"(rd::smem_addr(&bar))
+        : "memory");
+  const bool ok = rd::mbar_wait(&bar, 0, polls);
+  *status = !ok ? rd::kStTimeout : (copy && buf.x == src->x && buf.w == src->w) ? rd::kStOk : -1;
+}
+
+// Peak fused multiply-add rate: eight independent FMA chains per thread in
+// registers, enough warps to fill every scheduler; one value per thread is
+// stored so that nothing is optimised away.
+template <typename F>
+__global__ void __launch_bounds__(256) k_fma_probe(F* out, int iters) {
+  F a[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) a[j] = F(threadIdx.x + j) * F(1e-3);
+  const F b = F(0.999999), c = F(1e-6);
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) a[j] = fma(a[j], b, c);
+  }
+  F s = F(0);
+#pragma unroll
+  for (int j = 0; j < 8; ++j) s += a[j];
+  out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+template <typename F>
+rd_status fma_probe(double* tflops) {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return RD_ERR_CUDA;
+  const int blocks = sms * 8, threads = 256, iters = 1 << 14;
+  F* out = nullptr;
+  cudaStream_t s = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  rd_status st = RD_ERR_CUDA;
+  if (cudaMalloc(&out, sizeof(F) * size_t(blocks) * threads) == cudaSuccess &&
+      cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) == cudaSuccess && cudaEventCreate(&e0) == cudaSuccess &&
+      cudaEventCreate(&e1) == cudaSuccess) {
+    k_fma_probe<F><<<blocks, threads, 0, s>>>(out, iters);   // warm-up
+    cudaEventRecord(e0, s);
+    k_fma_probe<F><<<blocks, threads, 0, s>>>(out, iters);
+    cudaEventRecord(e1, s);
+    float ms = 0.f;
+    if (cudaGetLastError() == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess &&
+        cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms > 0.f) {
+      *tflops = 2.0 * 8.0 * iters * double(blocks) * threads / (1e-3 * ms) / 1e12;
+      st = RD_OK;
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (s) cudaStreamDestroy(s);
+  if (out) cudaFree(out);
+  cudaGetLastError();
+  return st;
+}
+
+// A field pointer (host or device) must be non-null and aligned to its
+// element (FP64): the kernels read caller fields with plain 8-byte loads, and
+// a misaligned device address would fault the context instead of failing
+// the call.
+bool bad_field(const void* p) { return !p || (reinterpret_cast<uintptr_t>(p) & 7u); }
+bool bad_opt_field(const void* p) { return p && (reinterpret_cast<uintptr_t>(p) & 7u); }
+// Host parameter vectors must be finite: a NaN weight of a Gaussian would
+// otherwise be dropped silently by the basis synthesis, which skips terms
+// below its cut-off.
+bool bad_vec(const double* v, int n) {
+  if (!v) return true;
+  for (int i = 0; i < n; ++i)
+    if (!std::isfinite(v[i])) return true;
+  return false;
+}
+}  // namespace
+
 extern "C" {
 
 rd_status rd_config_default(rd_config* c) {
@@ -1441,7 +1652,7 @@ rd_status rd_create(rd_ctx** out, const rd_config* cfg, int np, void* workspace,
 }
 
 rd_status rd_set_tissue(rd_ctx* c, const double* m_wm, const double* m_gm, const double* m_csf) {
-  if (!c || !m_wm || !m_gm || !m_csf) return RD_ERR_ARG;
+  if (!c || bad_field(m_wm) || bad_field(m_gm) || bad_field(m_csf)) return RD_ERR_ARG;
   return c->e->set_tissue(m_wm, m_gm, m_csf);
 }
 
@@ -1451,27 +1662,30 @@ rd_status rd_set_basis(rd_ctx* c, const double* centers, double sigma) {
 }
 
 rd_status rd_set_data(rd_ctx* c, const double* d) {
-  if (!c || !d) return RD_ERR_ARG;
+  if (!c || bad_field(d)) return RD_ERR_ARG;
   return c->e->set_data(d);
 }
 
 rd_status rd_coupling_field(rd_ctx* c, double* q_wm, double* q_gm, double* q_csf) {
-  if (!c || !q_wm || !q_gm || !q_csf) return RD_ERR_ARG;
+  if (!c || bad_field(q_wm) || bad_field(q_gm) || bad_field(q_csf)) return RD_ERR_ARG;
   return c->e->coupling_field(q_wm, q_gm, q_csf);
 }
 
 rd_status rd_forward(rd_ctx* c, const double* p, double k_f, double rho_f, double* c1_out, double* misfit) {
-  if (!c || !p || !(k_f >= 0) || !std::isfinite(rho_f)) return RD_ERR_ARG;
+  if (!c || bad_vec(p, c->e->np) || !(k_f >= 0) || !std::isfinite(k_f) || !std::isfinite(rho_f) ||
+      bad_opt_field(c1_out))
+    return RD_ERR_ARG;
   return c->e->forward(p, k_f, rho_f, c1_out, misfit);
 }
 
 rd_status rd_adjoint(rd_ctx* c, double* alpha0_out) {
-  if (!c) return RD_ERR_ARG;
+  if (!c || bad_opt_field(alpha0_out)) return RD_ERR_ARG;
   return c->e->adjoint(alpha0_out);
 }
 
 rd_status rd_gradient(rd_ctx* c, const double* p, double k_f, double rho_f, double* misfit, double* grad) {
-  if (!c || !p || !grad || !(k_f >= 0) || !std::isfinite(rho_f)) return RD_ERR_ARG;
+  if (!c || bad_vec(p, c->e->np) || !grad || !(k_f >= 0) || !std::isfinite(k_f) || !std::isfinite(rho_f))
+    return RD_ERR_ARG;
   if (!c->e->have_data) {
     snprintf(c->e->err, sizeof(c->e->err), "rd_set_data is required");
     return RD_ERR_STATE;
@@ -1495,7 +1709,9 @@ rd_status rd_last_gradient(const rd_ctx* c, double* grad) {
 }
 
 rd_status rd_hessvec(rd_ctx* c, const double* p, double k_f, double rho_f, const double* v, double* Hv) {
-  if (!c || !p || !v || !Hv || !(k_f >= 0) || !std::isfinite(rho_f)) return RD_ERR_ARG;
+  if (!c || bad_vec(p, c->e->np) || bad_vec(v, c->e->np + 2) || !Hv || !(k_f >= 0) || !std::isfinite(k_f) ||
+      !std::isfinite(rho_f))
+    return RD_ERR_ARG;
   if (!c->e->have_tissue || !c->e->have_basis) {
     snprintf(c->e->err, sizeof(c->e->err), "rd_set_tissue and rd_set_basis are required");
     return RD_ERR_STATE;
@@ -1504,7 +1720,7 @@ rd_status rd_hessvec(rd_ctx* c, const double* p, double k_f, double rho_f, const
 }
 
 rd_status rd_apply_operator(rd_ctx* c, double k_f, const double* u, double* Au) {
-  if (!c || !u || !Au || !std::isfinite(k_f)) return RD_ERR_ARG;
+  if (!c || bad_field(u) || bad_field(Au) || !std::isfinite(k_f)) return RD_ERR_ARG;
   return c->e->apply_operator(k_f, u, Au);
 }
 
@@ -1514,7 +1730,7 @@ rd_status rd_set_precond_scale(rd_ctx* c, double scale) {
 }
 
 rd_status rd_apply_precond(rd_ctx* c, double k_f, const double* r, double* z) {
-  if (!c || !r || !z || !(k_f >= 0)) return RD_ERR_ARG;
+  if (!c || bad_field(r) || bad_field(z) || !(k_f >= 0) || !std::isfinite(k_f)) return RD_ERR_ARG;
   return c->e->apply_precond(k_f, r, z);
 }
 
@@ -1568,7 +1784,7 @@ BatchGraph g_batch;
 }  // namespace
 
 rd_status rd_set_anatomy_data(rd_ctx* c, const double* md_wm, const double* md_gm, const double* md_csf) {
-  if (!c || !md_wm || !md_gm || !md_csf) return RD_ERR_ARG;
+  if (!c || bad_field(md_wm) || bad_field(md_gm) || bad_field(md_csf)) return RD_ERR_ARG;
   {
     // a batch graph captured before holds misfit launches without m_D
     std::lock_guard<std::mutex> lk(g_batch_mu);
@@ -1581,7 +1797,9 @@ rd_status rd_batch_gradient(rd_ctx* const* ctxs, int count, const double* const*
                             const double* rho_f, double* misfit, double* const* grad) {
   if (!ctxs || count < 1 || !p || !k_f || !rho_f || !grad) return RD_ERR_ARG;
   for (int i = 0; i < count; ++i) {
-    if (!ctxs[i] || !p[i] || !grad[i] || !(k_f[i] >= 0) || !std::isfinite(rho_f[i])) return RD_ERR_ARG;
+    if (!ctxs[i] || bad_vec(p[i], ctxs[i]->e->np) || !grad[i] || !(k_f[i] >= 0) || !std::isfinite(k_f[i]) ||
+        !std::isfinite(rho_f[i]))
+      return RD_ERR_ARG;
     rd::EngineBase* e = ctxs[i]->e;
     if (!e->have_tissue || !e->have_basis || !e->have_data) {
       snprintf(e->err, sizeof(e->err), "rd_set_tissue, rd_set_basis and rd_set_data are required");
@@ -1657,6 +1875,30 @@ rd_status rd_batch_gradient(rd_ctx* const* ctxs, int count, const double* const*
     if (s != RD_OK && (worst == RD_OK || worst == RD_ERR_NOCONV)) worst = s;
   }
   return worst;
+}
+
+rd_status rd_selftest_bounded_wait(unsigned polls, int copy, const void* src16, int* status, void* stream) {
+  if (!status || (reinterpret_cast<uintptr_t>(status) & 3u) || polls == 0 || polls > rd::kWaitLimit)
+    return RD_ERR_ARG;
+  if (copy && (!src16 || (reinterpret_cast<uintptr_t>(src16) & 15u))) return RD_ERR_ARG;
+  k_selftest_wait<<<1, 32, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
+      reinterpret_cast<const int4*>(copy ? src16 : nullptr), polls, copy, status);
+  return cudaGetLastError() == cudaSuccess ? RD_OK : RD_ERR_CUDA;
+}
+
+rd_status rd_active_tiles(const rd_ctx* c, long long* counts) {
+  if (!c || !counts) return RD_ERR_ARG;
+  if (!c->e->have_tissue) return RD_ERR_STATE;
+  for (int k = 0; k < 3; ++k) {
+    counts[2 * k] = c->e->active_tiles[k];
+    counts[2 * k + 1] = c->e->all_tiles[k];
+  }
+  return RD_OK;
+}
+
+rd_status rd_probe_fma_rate(int prec, double* tflops) {
+  if (!tflops || (prec != RD_FP64 && prec != RD_MIXED)) return RD_ERR_ARG;
+  return prec == RD_FP64 ? fma_probe<double>(tflops) : fma_probe<float>(tflops);
 }
 
 int rd_last_pcg_iters(const rd_ctx* c) { return c ? c->e->last_iters : 0; }

@@ -164,7 +164,7 @@ __device__ __forceinline__ void finalize(const Fin& f, const double* tots, int K
       st->total_it += 1;
       if (st->sticky == kStTimeout) {
         st->done = 1;
-      } else if (!isfinite(tot)) {
+      } else if (!isfinite(tot) || st->status == kStNonFinite) {
         st->done = 1;
         st->status = kStNonFinite;
       } else if (tot <= st->rtol2 * (st->bb > 0.0 ? st->bb : st->ff)) {

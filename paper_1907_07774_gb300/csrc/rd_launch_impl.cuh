@@ -162,6 +162,8 @@ cudaError_t Launch<T>::op(int L, const OpArgs<T>& a, cudaStream_t s) {
           t.prm = a.prm;
           t.st = a.fin.st;
           t.fin = a.fin;
+          t.tiles = a.tiles;
+          t.ntiles_act = a.ntiles_act;
           const long long tiles = (long long)(a.g.n[2] / TS::W) * (a.axis == 1 ? a.g.n[0] : a.g.n[1]);
           if constexpr (sizeof(T) == 4) {
             if (a.axis == 1)
@@ -291,6 +293,7 @@ cudaError_t Launch<T>::pcg_opx(int L, const PcgOpxArgs<T>& a, cudaStream_t s) {
           t.prm = a.prm;
           t.st = a.st;
           t.fin = a.fin;
+          t.rowact = a.rowact;
           return launch_tma(k_pcg_opx_tma<T, LL>, TS::OPX_SMEM, TS::THREADS, rows / TS::ROWS, t, s, kcPcgOpx);
         }
       }
@@ -323,6 +326,8 @@ cudaError_t Launch<T>::grad(int L, const GradArgs<T>& a, cudaStream_t s) {
           t.twA = a.twA;
           t.twB = a.twB;
           t.fin = a.fin;
+          t.tiles = a.tiles;
+          t.ntiles_act = a.ntiles_act;
           const long long tiles = (long long)(a.g.n[2] / TS::W) * (a.axis == 1 ? a.g.n[0] : a.g.n[1]);
           if (a.axis == 1) return launch_tma(k_grad_tma<T, LL, 1>, TS::GRAD_SMEM, TS::THREADS, tiles, t, s, kcGrad);
           return launch_tma(k_grad_tma<T, LL, 0>, TS::GRAD_SMEM, TS::THREADS, tiles, t, s, kcGrad);

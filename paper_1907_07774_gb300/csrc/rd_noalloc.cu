@@ -12,9 +12,11 @@
 //
 // The array is a fixed 128 KiB that every GPU loading this library holds
 // until process exit.  All calls share it and it keeps the previous call's
-// contents: each call rewrites the scalars and clears the reduction counter
-// before its kernels run.  Calls that overlap on the GPU (different streams,
-// or different host threads without ordering) race on this array.
+// contents: each call first runs a one-block kernel on the caller's stream
+// that rewrites the scalars, clears the solver state and clears the reduction
+// counters, so nothing of an earlier call is read.  Calls that overlap on the
+// GPU (different streams, or different host threads without ordering) race on
+// this array.
 #include <cmath>
 #include <cstddef>
 #include <cstring>
@@ -59,6 +61,17 @@ DeviceSlot g_slots[kMaxDevices];
 
 int length_index(int L) { return lidx(L); }
 
+// Start of a call: this call's scalars (passed by value, so no host buffer
+// is read by a copy), a cleared solver state and cleared counters.
+__global__ void k_static_begin(StaticScratch* d, Params prm) {
+  const int t = threadIdx.x;
+  if (t == 0) {
+    d->prm = prm;
+    memset(&d->st, 0, sizeof(PcgState));
+  }
+  if (t < 64) d->counter[t] = 0u;
+}
+
 // Once per device, with that device current: find the array's device
 // address (the host-side symbol is only a stand-in) and upload the twiddle
 // tables computed in FP64 on the host.
@@ -89,6 +102,13 @@ rd_status setup_device(int dev, StaticScratch** out) {
       return RD_ERR_CUDA;
     }
   }
+  // A copy from pageable host memory may return before the data reach the
+  // device, and it is ordered only with the legacy default stream; the
+  // caller's stream may be a non-blocking one.  Wait for the tables here.
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    cudaGetLastError();
+    return RD_ERR_CUDA;
+  }
   s.ptr = d;
   s.ready = true;
   *out = d;
@@ -101,7 +121,7 @@ rd_status setup_device(int dev, StaticScratch** out) {
 extern "C" rd_status rd_apply_precond_static(const int n[3], double coef, const double* r, double* z,
                                              void* stream) {
   using namespace rd;
-  if (!n || !r || !z || !(coef >= 0.0)) return RD_ERR_ARG;
+  if (!n || !r || !z || !std::isfinite(coef) || coef < 0.0) return RD_ERR_ARG;
   // the pencil kernels read and write pairs of values with 16-byte accesses
   if ((reinterpret_cast<uintptr_t>(r) & 15) || (reinterpret_cast<uintptr_t>(z) & 15)) return RD_ERR_ARG;
   for (int a = 0; a < 3; ++a)
@@ -122,11 +142,8 @@ extern "C" rd_status rd_apply_precond_static(const int n[3], double coef, const 
   prm.k_f = coef;
   prm.kbar1 = 1.0;
   prm.inv_nn = 1.0 / double(g.nn);
-  if (cudaMemcpyAsync(&d->prm, &prm, sizeof(Params), cudaMemcpyHostToDevice, st) != cudaSuccess ||
-      cudaMemsetAsync(&d->counter[0], 0, sizeof(d->counter), st) != cudaSuccess) {
-    cudaGetLastError();
-    return RD_ERR_CUDA;
-  }
+  k_static_begin<<<1, 64, 0, st>>>(d, prm);
+  if (cudaGetLastError() != cudaSuccess) return RD_ERR_CUDA;
   auto args = [&](int axis, const double* in, double* out) {
     DhtArgs<double> a;
     memset(&a, 0, sizeof(a));

@@ -175,6 +175,8 @@ struct OpArgs {
   const cpx<T>* twB;
   Params* prm;
   Fin fin;
+  const int* tiles;        // strided TMA passes: tiles where kappa is not
+  const int* ntiles_act;   // identically zero (null: all tiles)
 };
 
 template <typename T, int L, bool CONTIG>
@@ -336,6 +338,7 @@ struct PcgOpxArgs {
   Params* prm;
   PcgState* st;
   Fin fin;   // reduces |p|^2 and sum kappa (L d_2 p)^2 (kFinPqAdd)
+  const int* rowact;   // TMA row tiles: 0 where kappa vanishes on the tile (null: all)
 };
 
 template <typename T, int L>
@@ -420,6 +423,8 @@ struct GradArgs {
   const cpx<T>* twA;
   const cpx<T>* twB;
   Fin fin;
+  const int* tiles;        // as in OpArgs
+  const int* ntiles_act;
 };
 
 template <typename T, int L, bool CONTIG>

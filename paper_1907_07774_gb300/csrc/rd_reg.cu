@@ -527,6 +527,18 @@ struct rg_ctx {
   rd::RegBase* e;
 };
 
+namespace {
+// Field pointers (host or device) must be non-null and 8-byte aligned: the
+// kernels read them with plain FP64 loads.
+bool bad3(const double* const* f) {
+  if (!f) return true;
+  for (int k = 0; k < 3; ++k)
+    if (!f[k] || (reinterpret_cast<uintptr_t>(f[k]) & 7u)) return true;
+  return false;
+}
+bool bad1(const void* p) { return !p || (reinterpret_cast<uintptr_t>(p) & 7u); }
+}  // namespace
+
 extern "C" {
 
 rd_status rg_config_default(rg_config* cfg) {
@@ -558,43 +570,32 @@ rd_status rg_create(rg_ctx** out, const rg_config* cfg, void* stream) {
 
 rd_status rg_set_images(rg_ctx* c, const double* const* ma, const double* const* mp, const double* c1,
                         const double* const* q) {
-  if (!c || !ma || !mp || !c1) return RD_ERR_ARG;
-  for (int k = 0; k < 3; ++k)
-    if (!ma[k] || !mp[k] || (q && !q[k])) return RD_ERR_ARG;
+  if (!c || bad3(ma) || bad3(mp) || bad1(c1) || (q && bad3(q))) return RD_ERR_ARG;
   return c->e->set_images(ma, mp, c1, q);
 }
 
 rd_status rg_forward(rg_ctx* c, const double* const* v, double* const* m1, double* J) {
-  if (!c || !v || !v[0] || !v[1] || !v[2]) return RD_ERR_ARG;
-  if (m1 && (!m1[0] || !m1[1] || !m1[2])) return RD_ERR_ARG;
+  if (!c || bad3(v) || (m1 && bad3(m1))) return RD_ERR_ARG;
   return c->e->forward(v, m1, J);
 }
 
 rd_status rg_gradient(rg_ctx* c, const double* const* v, double* J, double* const* g) {
-  if (!c || !v || !g) return RD_ERR_ARG;
-  for (int k = 0; k < 3; ++k)
-    if (!v[k] || !g[k]) return RD_ERR_ARG;
+  if (!c || bad3(v) || bad3(g)) return RD_ERR_ARG;
   return c->e->gradient(v, J, g);
 }
 
 rd_status rg_hessvec(rg_ctx* c, const double* const* v, const double* const* vt, double* const* hv) {
-  if (!c || !v || !vt || !hv) return RD_ERR_ARG;
-  for (int k = 0; k < 3; ++k)
-    if (!v[k] || !vt[k] || !hv[k]) return RD_ERR_ARG;
+  if (!c || bad3(v) || bad3(vt) || bad3(hv)) return RD_ERR_ARG;
   return c->e->hessvec(v, vt, hv);
 }
 
 rd_status rg_apply_precond(rg_ctx* c, const double* const* r, double* const* z) {
-  if (!c || !r || !z) return RD_ERR_ARG;
-  for (int k = 0; k < 3; ++k)
-    if (!r[k] || !z[k]) return RD_ERR_ARG;
+  if (!c || bad3(r) || bad3(z)) return RD_ERR_ARG;
   return c->e->precond(r, z);
 }
 
 rd_status rg_project(rg_ctx* c, const double* const* w, double* const* kw) {
-  if (!c || !w || !kw) return RD_ERR_ARG;
-  for (int k = 0; k < 3; ++k)
-    if (!w[k] || !kw[k]) return RD_ERR_ARG;
+  if (!c || bad3(w) || bad3(kw)) return RD_ERR_ARG;
   return c->e->project(w, kw);
 }
 

@@ -32,10 +32,10 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
                : "memory");
 }
 
-// Waits for phase `parity` of the barrier; false after kWaitLimit polls.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+// Waits for phase `parity` of the barrier; false after `limit` polls.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, unsigned limit = kWaitLimit) {
   const uint32_t a = smem_addr(bar);
-  for (unsigned it = 0; it < kWaitLimit; ++it) {
+  for (unsigned it = 0; it < limit; ++it) {
     uint32_t ok;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -171,6 +171,11 @@ struct OpTmaArgs {
   Params* prm;
   PcgState* st;
   Fin fin;
+  // Optional list of the tiles to process (device; null = every tile) and
+  // its length (device).  Tiles where kappa vanishes identically contribute
+  // exactly zero to d_axis(kappa d_axis u) and are left out of the list.
+  const int* tiles;
+  const int* ntiles_act;
 };
 
 // q <- q + coef * d_axis(kappa d_axis u), coef = c0 (k_f) s; optionally
@@ -198,7 +203,9 @@ __global__ void __launch_bounds__(TmaShape<T, L>::THREADS) k_op_tma(const __grid
   __shared__ uint64_t ubar, kbar, qbar;
   const int g = threadIdx.x / TH, t = threadIdx.x % TH;
   cpx<T>* sm = xbuf + g * S::XSTRIDE;
-  const long long ntiles = (long long)(a.g.n[2] / S::W) * (AXIS == 1 ? a.g.n[0] : a.g.n[1]);
+  const long long ntiles =
+      a.tiles ? (long long)*a.ntiles_act : (long long)(a.g.n[2] / S::W) * (AXIS == 1 ? a.g.n[0] : a.g.n[1]);
+  auto tile_at = [&](long long j) { return a.tiles ? (long long)a.tiles[j] : j; };
   const T coef = T(a.c0 * (a.use_kf ? a.prm->k_f : 1.0) * a.prm->s / (double(L) * double(L)));
 
   TmaPending pu, pk, pq;
@@ -219,15 +226,16 @@ __global__ void __launch_bounds__(TmaShape<T, L>::THREADS) k_op_tma(const __grid
   __syncthreads();
   const long long t0 = blockIdx.x, stride = gridDim.x;
   if (threadIdx.x == 0 && t0 < ntiles) {
-    issue(u_buf, &a.map_u, &ubar, pu, t0);
-    issue(k_buf, &a.map_k, &kbar, pk, t0);
-    issue(q_buf, &a.map_q, &qbar, pq, t0);
+    issue(u_buf, &a.map_u, &ubar, pu, tile_at(t0));
+    issue(k_buf, &a.map_k, &kbar, pk, tile_at(t0));
+    issue(q_buf, &a.map_q, &qbar, pq, tile_at(t0));
   }
   double red = 0.0;
   bool bad = false;
   int i = 0;
-  for (long long tile = t0; tile < ntiles; tile += stride, ++i) {
-    const bool more = tile + stride < ntiles;
+  for (long long j = t0; j < ntiles; j += stride, ++i) {
+    const long long tile = tile_at(j);
+    const bool more = j + stride < ntiles;
     bool ok = mbar_wait(&ubar, i & 1);
     if (__syncthreads_or(!ok)) { bad = true; break; }
     ++pu.done;
@@ -236,7 +244,7 @@ __global__ void __launch_bounds__(TmaShape<T, L>::THREADS) k_op_tma(const __grid
     for (int r = 0; r < R; ++r) v[r] = *tile_pair<T>(u_buf, idx_a<L>(r, t), g);
     __syncthreads();   // every u value is in registers
     if (threadIdx.x == 0) {
-      if (more) issue(u_buf, &a.map_u, &ubar, pu, tile + stride);
+      if (more) issue(u_buf, &a.map_u, &ubar, pu, tile_at(j + stride));
       if (i > 0) {
         // q_buf is free once the previous tile's store has read it
         bulk_wait_read0();
@@ -260,7 +268,7 @@ __global__ void __launch_bounds__(TmaShape<T, L>::THREADS) k_op_tma(const __grid
     }
     red += double(loc);
     __syncthreads();   // every kappa value is in registers
-    if (threadIdx.x == 0 && more) issue(k_buf, &a.map_k, &kbar, pk, tile + stride);
+    if (threadIdx.x == 0 && more) issue(k_buf, &a.map_k, &kbar, pk, tile_at(j + stride));
     fft_ab<T, L, -1, true>(v, sm, t, twA);
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = times_ik(v[r], kwave<L>(idx_b<L>(r, t)));
@@ -324,7 +332,9 @@ __global__ void __launch_bounds__(TmaShape<T, L>::THREADS) k_op_tma_red(const __
   __shared__ uint64_t ubar, kbar;
   const int g = threadIdx.x / TH, t = threadIdx.x % TH;
   cpx<T>* sm = xbuf + g * S::XSTRIDE;
-  const long long ntiles = (long long)(a.g.n[2] / S::W) * (AXIS == 1 ? a.g.n[0] : a.g.n[1]);
+  const long long ntiles =
+      a.tiles ? (long long)*a.ntiles_act : (long long)(a.g.n[2] / S::W) * (AXIS == 1 ? a.g.n[0] : a.g.n[1]);
+  auto tile_at = [&](long long j) { return a.tiles ? (long long)a.tiles[j] : j; };
   const T coef = T(a.c0 * (a.use_kf ? a.prm->k_f : 1.0) * a.prm->s / (double(L) * double(L)));
   TmaPending pu, pk;
   auto issue = [&](unsigned char* dst, const CUtensorMap* map, uint64_t* bar, TmaPending& pd, long long tile) {
@@ -342,14 +352,15 @@ __global__ void __launch_bounds__(TmaShape<T, L>::THREADS) k_op_tma_red(const __
   __syncthreads();
   const long long t0 = blockIdx.x, stride = gridDim.x;
   if (threadIdx.x == 0 && t0 < ntiles) {
-    issue(u_buf, &a.map_u, &ubar, pu, t0);
-    issue(k_buf, &a.map_k, &kbar, pk, t0);
+    issue(u_buf, &a.map_u, &ubar, pu, tile_at(t0));
+    issue(k_buf, &a.map_k, &kbar, pk, tile_at(t0));
   }
   double red = 0.0;
   bool bad = false;
   int i = 0;
-  for (long long tile = t0; tile < ntiles; tile += stride, ++i) {
-    const bool more = tile + stride < ntiles;
+  for (long long j = t0; j < ntiles; j += stride, ++i) {
+    const long long tile = tile_at(j);
+    const bool more = j + stride < ntiles;
     bool ok = mbar_wait(&ubar, i & 1);
     if (__syncthreads_or(!ok)) { bad = true; break; }
     ++pu.done;
@@ -357,7 +368,7 @@ __global__ void __launch_bounds__(TmaShape<T, L>::THREADS) k_op_tma_red(const __
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = *tile_pair<T>(u_buf, idx_a<L>(r, t), g);
     __syncthreads();   // every u value is in registers
-    if (threadIdx.x == 0 && more) issue(u_buf, &a.map_u, &ubar, pu, tile + stride);
+    if (threadIdx.x == 0 && more) issue(u_buf, &a.map_u, &ubar, pu, tile_at(j + stride));
     fft_ab<T, L, -1, true>(v, sm, t, twA);
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = times_ik(v[r], kwave<L>(idx_b<L>(r, t)));
@@ -389,7 +400,7 @@ __global__ void __launch_bounds__(TmaShape<T, L>::THREADS) k_op_tma_red(const __
       tma_reduce_add3(&a.map_q, k_buf, c0, c1, c2);
       bulk_commit();
       bulk_wait_read0();
-      if (more) issue(k_buf, &a.map_k, &kbar, pk, tile + stride);
+      if (more) issue(k_buf, &a.map_k, &kbar, pk, tile_at(j + stride));
     }
   }
   if (threadIdx.x == 0) bulk_wait0();
@@ -534,6 +545,8 @@ struct GradTmaArgs {
   const cpx<T>* twA;
   const cpx<T>* twB;
   Fin fin;
+  const int* tiles;        // as in OpTmaArgs: tiles where kappa is not zero
+  const int* ntiles_act;
 };
 
 // Gradient pass along a strided axis (the reduction of k_grad without the
@@ -558,7 +571,9 @@ __global__ void __launch_bounds__(TmaShape<T, L>::THREADS) k_grad_tma(const __gr
   __shared__ uint64_t abar, bbar, cbar;
   const int g = threadIdx.x / TH, t = threadIdx.x % TH;
   cpx<T>* sm = xbuf + g * S::XSTRIDE;
-  const long long ntiles = (long long)(a.g.n[2] / S::W) * (AXIS == 1 ? a.g.n[0] : a.g.n[1]);
+  const long long ntiles =
+      a.tiles ? (long long)*a.ntiles_act : (long long)(a.g.n[2] / S::W) * (AXIS == 1 ? a.g.n[0] : a.g.n[1]);
+  auto tile_at = [&](long long j) { return a.tiles ? (long long)a.tiles[j] : j; };
   const T scale = T(1.0 / (double(L) * double(L)));
   const bool two = a.has_u1 != 0;
   TmaPending pa, pb, pc;
@@ -578,15 +593,16 @@ __global__ void __launch_bounds__(TmaShape<T, L>::THREADS) k_grad_tma(const __gr
   __syncthreads();
   const long long t0 = blockIdx.x, stride = gridDim.x;
   if (threadIdx.x == 0 && t0 < ntiles) {
-    issue(a_buf, &a.map_u0, &abar, pa, t0);
-    if (two) issue(b_buf, &a.map_u1, &bbar, pb, t0);
-    issue(c_buf, &a.map_w, &cbar, pc, t0);
+    issue(a_buf, &a.map_u0, &abar, pa, tile_at(t0));
+    if (two) issue(b_buf, &a.map_u1, &bbar, pb, tile_at(t0));
+    issue(c_buf, &a.map_w, &cbar, pc, tile_at(t0));
   }
   double red = 0.0;
   bool bad = false;
   int i = 0;
-  for (long long tile = t0; tile < ntiles; tile += stride, ++i) {
-    const bool more = tile + stride < ntiles;
+  for (long long j = t0; j < ntiles; j += stride, ++i) {
+    const long long tile = tile_at(j);
+    const bool more = j + stride < ntiles;
     // u0 is load 2i of barrier A (parity 0), kappa load 2i + 1 (parity 1)
     bool ok = mbar_wait(&abar, 0);
     if (two) ok = ok && mbar_wait(&bbar, i & 1);
@@ -602,7 +618,7 @@ __global__ void __launch_bounds__(TmaShape<T, L>::THREADS) k_grad_tma(const __gr
     __syncthreads();   // every u0 and u1 value is in registers
     if (threadIdx.x == 0) {
       issue(a_buf, &a.map_k, &abar, pa, tile);
-      if (two && more) issue(b_buf, &a.map_u1, &bbar, pb, tile + stride);
+      if (two && more) issue(b_buf, &a.map_u1, &bbar, pb, tile_at(j + stride));
     }
     fft_ab<T, L, -1, true>(du, sm, t, twA);
 #pragma unroll
@@ -615,7 +631,7 @@ __global__ void __launch_bounds__(TmaShape<T, L>::THREADS) k_grad_tma(const __gr
 #pragma unroll
     for (int r = 0; r < R; ++r) dw[r] = *tile_pair<T>(c_buf, idx_a<L>(r, t), g);
     __syncthreads();   // every w value is in registers
-    if (threadIdx.x == 0 && more) issue(c_buf, &a.map_w, &cbar, pc, tile + stride);
+    if (threadIdx.x == 0 && more) issue(c_buf, &a.map_w, &cbar, pc, tile_at(j + stride));
     fft_ab<T, L, -1, true>(dw, sm, t, twA);
 #pragma unroll
     for (int r = 0; r < R; ++r) dw[r] = times_ik(dw[r], kwave<L>(idx_b<L>(r, t)));
@@ -631,7 +647,7 @@ __global__ void __launch_bounds__(TmaShape<T, L>::THREADS) k_grad_tma(const __gr
     }
     red += double(loc * scale);
     __syncthreads();   // every kappa value is in registers
-    if (threadIdx.x == 0 && more) issue(a_buf, &a.map_u0, &abar, pa, tile + stride);
+    if (threadIdx.x == 0 && more) issue(a_buf, &a.map_u0, &abar, pa, tile_at(j + stride));
   }
   if (bad) {
     if (threadIdx.x == 0) {
@@ -813,6 +829,10 @@ struct PcgOpxTmaArgs {
   Params* prm;
   PcgState* st;
   Fin fin;   // reduces |p|^2 and sum kappa (L d_2 p)^2 (kFinPqAdd)
+  // Optional flag per row tile (device; null = all set): 0 when kappa
+  // vanishes on every row of the tile, where q = p exactly and the
+  // operator's transforms are skipped.
+  const int* rowact;
 };
 
 // z = H_2(w); p = z + beta p; q = p - s k_f d_2(kappa d_2 p)  (fields written
@@ -859,9 +879,15 @@ __global__ void __launch_bounds__(TmaRowShape<T, L>::THREADS) k_pcg_opx_tma(cons
   }
   __syncthreads();
   const long long t0 = blockIdx.x, stride = gridDim.x;
+  // next tile of this block's sequence, from `from` on, whose kappa is needed
+  auto next_act = [&](long long from) {
+    while (from < ntiles && a.rowact && !a.rowact[from]) from += stride;
+    return from;
+  };
   if (threadIdx.x == 0 && t0 < ntiles) {
     issue(w_buf, &a.map_w, &wbar, pw, t0);
-    issue(k_buf, &a.map_k, &kbar, pk, t0);
+    const long long kt = next_act(t0);
+    if (kt < ntiles) issue(k_buf, &a.map_k, &kbar, pk, kt);
     if (use_p) issue(p_buf, &a.map_p, &pbar, pp, t0);
   }
   bool bad = false;
@@ -870,6 +896,7 @@ __global__ void __launch_bounds__(TmaRowShape<T, L>::THREADS) k_pcg_opx_tma(cons
   const int ra = 2 * g, rb = 2 * g + 1;
   for (long long tile = t0; tile < ntiles; tile += stride, ++i) {
     const bool more = tile + stride < ntiles;
+    const bool act = !a.rowact || a.rowact[tile] != 0;
     T* prow_a = a.p + (tile * S::ROWS + ra) * L;
     T* prow_b = a.p + (tile * S::ROWS + rb) * L;
     T* qrow_a = a.q + (tile * S::ROWS + ra) * L;
@@ -915,13 +942,13 @@ __global__ void __launch_bounds__(TmaRowShape<T, L>::THREADS) k_pcg_opx_tma(cons
     // transform code (a loop that is not unrolled keeps the kernel small
     // enough for the instruction cache)
 #pragma unroll 1
-    for (int pass = 0; pass < 2; ++pass) {
+    for (int pass = 0; pass < (act ? 2 : 0); ++pass) {
       fft_ba<T, L, -1, true>(v, sm, t, twB);
 #pragma unroll
       for (int r = 0; r < R; ++r) v[r] = times_ik(v[r], kwave<L>(idx_a<L>(r, t)));
       fft_ab<T, L, +1, true>(v, sm, t, twA);
       if (pass == 1) break;
-      ok = mbar_wait(&kbar, i & 1);
+      ok = mbar_wait(&kbar, pk.done & 1);
       if (__syncthreads_or(!ok)) { bad = true; break; }
       ++pk.done;
 #pragma unroll
@@ -932,12 +959,19 @@ __global__ void __launch_bounds__(TmaRowShape<T, L>::THREADS) k_pcg_opx_tma(cons
         v[r].x *= ka;
         v[r].y *= kb;
       }
-      red_pp += double(lpp);
-      red_k += double(lk);
       __syncthreads();   // every kappa value is in registers
-      if (threadIdx.x == 0 && more) issue(k_buf, &a.map_k, &kbar, pk, tile + stride);
+      if (threadIdx.x == 0) {
+        const long long kt = next_act(tile + stride);
+        if (kt < ntiles) issue(k_buf, &a.map_k, &kbar, pk, kt);
+      }
     }
     if (bad) break;
+    red_pp += double(lpp);
+    red_k += double(lk);
+    if (!act) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[r] = {T(0), T(0)};
+    }
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const int n = idx_b<L>(r, t);

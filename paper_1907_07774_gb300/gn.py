@@ -67,7 +67,7 @@ def project(theta):
 
 
 def gauss_newton(solver, theta0, iters=10, cg_maxit=20, armijo_c=1e-4, max_backtracks=12, gtol=1e-6,
-                 forcing=None, scale=None, callback=None):
+                 forcing=None, scale=None, callback=None, fixed=()):
     """Run ``iters`` Gauss-Newton iterations from ``theta0 = [p, k_f, rho_f]``
     with a context that has tissue, basis and data set.
 
@@ -76,7 +76,11 @@ def gauss_newton(solver, theta0, iters=10, cg_maxit=20, armijo_c=1e-4, max_backt
     of magnitude), i.e. on S H S with S = diag(scale).  ``forcing``: CG
     relative tolerance; None gives Eisenstat-Walker
     ``min(0.5, sqrt(|g| / |g_0|))``, a number fixes it (with ``cg_maxit``
-    the Newton step then uses up to that many Hessian-vector products)."""
+    the Newton step then uses up to that many Hessian-vector products).
+    ``fixed``: indices of parameters held at their start value (their scale
+    is set to 0, so neither the gradient nor the step moves them); e.g.
+    ``fixed=(n_p + 1,)`` keeps rho_f, as the paper does for its inversions
+    (Sec. 1.2: inverting for every growth parameter at once is ill-posed)."""
     npar = solver.np
     theta = np.asarray(theta0, dtype=np.float64).copy()
     split = lambda th: (th[:npar], th[npar], th[npar + 1])
@@ -84,14 +88,16 @@ def gauss_newton(solver, theta0, iters=10, cg_maxit=20, armijo_c=1e-4, max_backt
         scale = np.ones_like(theta)
         scale[npar] = max(abs(theta[npar]), 1e-3)
         scale[npar + 1] = max(abs(theta[npar + 1]), 1e-3)
-    scale = np.asarray(scale, dtype=np.float64)
+    scale = np.asarray(scale, dtype=np.float64).copy()
+    for i in fixed:
+        scale[i] = 0.0
     J, g = solver.rd_gradient(*split(theta))
     g0 = float(np.linalg.norm(scale * g))
     hist = []
     for k in range(iters):
         t0 = time.perf_counter()
-        gn = float(np.linalg.norm(g))
         gs = scale * g
+        gn = float(np.linalg.norm(g[scale != 0.0]))
         if gn <= gtol or float(np.linalg.norm(gs)) <= 1e-12 * max(g0, 1e-300):
             break
         if forcing is None:
@@ -102,7 +108,8 @@ def gauss_newton(solver, theta0, iters=10, cg_maxit=20, armijo_c=1e-4, max_backt
         d = scale * ds
         slope = float(g @ d)
         if slope >= 0.0:
-            d, slope = -g, -gn * gn
+            d = -(scale != 0.0) * g
+            slope = -gn * gn
         step, accepted, n_ls = 1.0, False, 0
         for _ in range(max_backtracks):
             trial = project(theta + step * d)
@@ -129,7 +136,7 @@ def gauss_newton(solver, theta0, iters=10, cg_maxit=20, armijo_c=1e-4, max_backt
         theta = trial
         J = Jt
         g = solver.rd_adjoint()          # adjoint of the accepted trial's forward solve
-        rec = {"iter": k, "misfit": J, "grad_norm": float(np.linalg.norm(g)), "step": step,
+        rec = {"iter": k, "misfit": J, "grad_norm": float(np.linalg.norm(g[scale != 0.0])), "step": step,
                "hessvecs": n_hv, "line_search": n_ls, "seconds": time.perf_counter() - t0}
         hist.append(rec)
         if callback:

@@ -71,6 +71,9 @@ def lib():
         "rd_last_error": ([vp], ctypes.c_char_p),
         "rd_destroy": ([vp], None),
         "rd_apply_precond_static": ([vp, cd, vp, vp, vp], st),
+        "rd_selftest_bounded_wait": ([ctypes.c_uint, ci, vp, vp, vp], st),
+        "rd_probe_fma_rate": ([ci, _c_double_p], st),
+        "rd_active_tiles": ([vp, vp], st),
         "rd_profile_enable": ([ci], None),
         "rd_profile_read": ([vp, vp, ci], ci),
         "rd_profile_class": ([ci], ctypes.c_char_p),
@@ -108,6 +111,26 @@ def rd_apply_precond_static(n, coef, r, z, stream=None):
     (a, ka), (b, kb) = _ptr(r), _ptr(z)
     st = stream if stream is not None else torch.cuda.current_stream()
     return lib().rd_apply_precond_static(dims, float(coef), a, b, ctypes.c_void_p(st.cuda_stream))
+
+
+def rd_selftest_bounded_wait(polls, copy, src16, status, stream=None):
+    """Self-test of the bounded device-side wait (see include/rd.h): src16 a
+    16-byte CUDA tensor or None, status a one-element int32 CUDA tensor.
+    Returns the status code of the launch."""
+    import torch
+    st = stream if stream is not None else torch.cuda.current_stream()
+    src = src16.data_ptr() if src16 is not None else None
+    ptr = status.data_ptr() if status is not None else None
+    return lib().rd_selftest_bounded_wait(int(polls), int(copy), src, ptr, ctypes.c_void_p(st.cuda_stream))
+
+
+def rd_probe_fma_rate(prec="fp64"):
+    """Measured FMA rate of the current device in TFLOP/s (see include/rd.h)."""
+    v = ctypes.c_double(0.0)
+    status = lib().rd_probe_fma_rate(RD_FP64 if prec == "fp64" else RD_MIXED, ctypes.byref(v))
+    if status != RD_OK:
+        raise RDError(status, "FMA probe failed")
+    return v.value
 
 
 class RDError(RuntimeError):
@@ -284,6 +307,13 @@ class Context:
         (a, ka), (b, kb) = _ptr(r), _ptr(out)
         self._call(lib().rd_apply_precond(self.h, float(k_f), a, b))
         return out
+
+    def rd_active_tiles(self):
+        """{"axis0": (active, all), "axis1": (...), "rows": (...)}: tiles of the
+        operator passes where kappa1 is not identically zero."""
+        c = (ctypes.c_longlong * 6)()
+        self._call(lib().rd_active_tiles(self.h, c))
+        return {"axis0": (c[0], c[1]), "axis1": (c[2], c[3]), "rows": (c[4], c[5])}
 
     def rd_last_pcg_iters(self):
         return lib().rd_last_pcg_iters(self.h)

@@ -87,3 +87,17 @@ def test_registration_config_and_argument_checks(lib):
     assert L.rg_create(ctypes.byref(h), ctypes.byref(cfg), None) == 1
     assert not h.value
     assert L.rg_gradient(None, None, None, None) == 1
+
+
+def test_argument_checks_of_the_context_free_entry_points(lib):
+    """Both context-free entry points reject bad arguments before touching a
+    device (no GPU needed)."""
+    assert lib.rd_selftest_bounded_wait(100, 0, None, None, None) == 1        # no status buffer
+    assert lib.rd_selftest_bounded_wait(0, 0, None, 16, None) == 1            # zero polls
+    assert lib.rd_selftest_bounded_wait(100, 0, None, 18, None) == 1          # status misaligned
+    assert lib.rd_selftest_bounded_wait(100, 1, 24, 16, None) == 1            # source misaligned
+    assert lib.rd_selftest_bounded_wait(1 << 27, 0, None, 16, None) == 1      # above the passes' limit
+    dims = (ctypes.c_int * 3)(8, 8, 8)
+    assert lib.rd_apply_precond_static(dims, 0.1, None, None, None) == 1
+    assert lib.rd_apply_precond_static(dims, float("inf"), 16, 32, None) == 1
+    assert lib.rd_apply_precond_static(dims, 0.1, 8, 32, None) == 1          # 16-byte alignment

@@ -45,3 +45,30 @@ def test_committed_summary_names_a_captured_kernel_class():
     assert len(d["csrc_hash"]) == 16
     for ent in d["classes"].values():
         assert ent["bytes_per_launch"] > 0 and ent["cells"] > 0 and ent["kernel"]
+
+
+def test_oracle_work_comes_from_the_stored_oracle_run(tmp_path, monkeypatch):
+    """The CPU baseline scales its per-iteration sample by the oracle's own PCG
+    work, read from the stored full oracle run; without one there is none."""
+    monkeypatch.setattr(bench, "GOLDEN", str(tmp_path))
+    assert bench.oracle_work(256, 32) is None
+    run = {"pcg_iters_forward": [3, 4, 5], "pcg_iters_adjoint": [20, 21, 22], "seconds_gradient": 9.0}
+    (tmp_path / "oracle_full_work256_nt32_rtol1e-6.json").write_text(json.dumps(run))
+    w = bench.oracle_work(256, 32)
+    assert w["iters"] == 75 and w["solves"] == 6
+    v, t = bench.cpu_cells_per_s(256, 32, 2.0, 0.5, w["iters"], w["solves"])
+    assert t == 75 * 2.5 + 6 * 2.5 + 32 * 0.75 * 2.0
+    assert v == 256 ** 3 * 32 / t
+
+
+def test_reference_arm_without_stored_work_prints_unavailable(tmp_path, monkeypatch, capsys):
+    import argparse
+    monkeypatch.setattr(bench, "GOLDEN", str(tmp_path))
+    args = argparse.Namespace(n=256, nt=32, warmup=1, steps=1, gpus=1)
+    assert bench.run_reference(args, 0, 1) == 0
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and "unavailable" in line
+
+
+def test_cpu_model_is_a_string():
+    assert isinstance(bench.cpu_model(), str) and bench.cpu_model()

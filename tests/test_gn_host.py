@@ -109,3 +109,20 @@ def test_non_finite_trial_solves_are_rejected_steps():
     res = gn.gauss_newton(prob, th0, iters=30, cg_maxit=20)
     assert res.history[0]["step"] == 0.5 and res.history[0]["line_search"] == 2
     assert res.misfit < 1e-6 * J0
+
+
+def test_fixed_parameter_stays_and_the_rest_solves_the_reduced_problem():
+    """With rho_f held (the paper's protocol: invert for p and k_f at a fixed
+    proliferation rate) the loop leaves it untouched and converges to the
+    least-squares solution over the other parameters."""
+    rng = np.random.default_rng(4)
+    A = rng.standard_normal((30, 5))
+    b = rng.standard_normal(30)
+    prob = LeastSquares(lambda th: A @ th - b, lambda th: A, 3)
+    th0 = np.array([0.1, 0.2, 0.3, 0.4, 2.5])
+    res = gn.gauss_newton(prob, th0, iters=30, cg_maxit=20, fixed=(4,))
+    assert res.theta[4] == 2.5
+    free = A[:, :4]
+    want = np.linalg.lstsq(free, b - A[:, 4] * 2.5, rcond=None)[0]
+    if want[3] >= 0:                                      # k_f bound inactive
+        assert np.allclose(res.theta[:4], want, atol=1e-8)

@@ -110,6 +110,32 @@ def test_operator_and_preconditioner_at_256_match_oracle():
         del ctx
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_operator_where_kappa_vanishes_on_whole_tiles(prec):
+    """The TMA operator passes visit only the tiles where kappa is not
+    identically zero: kappa zero on a slab and on the whole box (no tile left),
+    and nonzero only on one column of voxels, against the oracle."""
+    n = (64, 32, 64)
+    x0, x1, x2 = coords(n)
+    rng = np.random.default_rng(5)
+    u = rng.standard_normal(n)
+    smooth = (1.2 + np.cos(x0) * np.sin(2 * x1) * np.cos(x2)) * np.ones(n)
+    cases = {"slab": smooth * (np.abs(x0 - np.pi) < 1.0),
+             "zero": np.zeros(n),
+             "column": np.where((np.abs(x1 - np.pi) < 0.1) & (np.abs(x2 - 1.0) < 0.1), smooth, 0.0)}
+    zero = np.zeros(n)
+    for name, m in cases.items():
+        ctx = R.Context(n, 4, 1, prec=prec, k_w=(1, 0, 0), rho_w=(1, 0, 0))
+        ctx.rd_set_tissue(m, zero, zero)
+        out = np.full(n, np.nan)
+        ctx.rd_apply_operator(0.3, u, out)
+        want = orc.Spectral(n, "numpy").A(u, 0.3 * m)
+        if name == "zero":
+            assert np.all(out == 0.0), name
+        else:
+            assert rel(out, want) <= TOL[prec] * (10 if prec == "fp64" else 1), name
+
+
 # ---------------------------------------------------------------- solves
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 @pytest.mark.parametrize("n,nt", [((16, 16, 16), 4), ((8, 16, 32), 3), ((8, 8, 8), 2), ((32, 96, 16), 3)])
