@@ -237,14 +237,22 @@ void rd_profile_enable(int on);
 int rd_profile_read(double* ms, long long* launches, int n);
 const char* rd_profile_class(int i);
 
-/* Autotuner: on this context's grid, time `reps` PCG iterations for each
- * candidate persistent-grid size (all resident blocks, or 1..8 blocks per
- * SM) and keep the fastest per kernel class; the choice applies to every
- * later launch in the process.  caps (may be NULL) receives, per class of
- * rd_profile_class, the chosen block count (0 = all resident blocks).
- * Leaves the PCG work fields modified (not the state, data or trajectory). */
-rd_status rd_autotune(rd_ctx* ctx, int reps, int* caps, int ncaps);
-/* Forget every autotuner choice (back to all resident blocks). */
+/* Autotuner (no counterpart in the paper): on this context's grid, time
+ * `reps` PCG iterations for every candidate of each kernel class of the PCG
+ * loop and keep the fastest, per kernel class and pencil length.  Candidates
+ * are the tile shape -- the TMA tile kernel (64-byte column tiles along the
+ * strided axes, whole-row tiles along the contiguous one, staged in shared
+ * memory) or the pencil kernel (256-thread blocks of pencil groups with
+ * direct loads) -- times the persistent grid size (all resident blocks, or
+ * 1..8 blocks per SM).  The choice applies to every later launch in the
+ * process for that class and length, so contexts of other grid sizes keep
+ * their own.  caps / pencil (may be NULL) receive, for the first ncaps
+ * classes of rd_profile_class, the chosen block count (0 = all resident
+ * blocks) and tile shape (1 = pencil kernel) for this grid's contiguous-axis
+ * length.  Leaves the PCG work fields modified (not the state, data or
+ * trajectory). */
+rd_status rd_autotune(rd_ctx* ctx, int reps, int* caps, int* pencil, int ncaps);
+/* Forget every autotuner choice (back to TMA tiles and all resident blocks). */
 void rd_autotune_clear(void);
 
 /* Message of the last failing call ("" if none). */

@@ -146,12 +146,25 @@ bool row_map(CUtensorMap* out, const void* ptr, const Geom& g, int esz, int rows
 
 bool prof_active() { return prof().on; }
 
+// Bumped by every change of an autotuner choice: graphs captured before
+// hold the old kernels and are rebuilt.
+std::atomic<int> g_tune_gen{0};
+
 namespace {
-std::atomic<int> g_tuned_cap[kcCount];
+// (cap << 1) | pencil per kernel class and pencil length
+std::atomic<int> g_tuned[kcCount][kNumL];
+bool tuned_key(int cls, int L) { return cls >= 0 && cls < kcCount && L >= 8 && L <= 256; }
 }
-int tuned_cap(int cls) { return (cls >= 0 && cls < kcCount) ? g_tuned_cap[cls].load() : 0; }
-void set_tuned_cap(int cls, int cap) {
-  if (cls >= 0 && cls < kcCount) g_tuned_cap[cls].store(cap < 0 ? 0 : cap);
+int tuned_cap(int cls, int L) { return tuned_key(cls, L) ? (g_tuned[cls][lidx(L)].load() >> 1) : 0; }
+bool tuned_pencil(int cls, int L) { return tuned_key(cls, L) && (g_tuned[cls][lidx(L)].load() & 1); }
+void set_tuned(int cls, int L, int cap, bool pencil) {
+  if (tuned_key(cls, L)) g_tuned[cls][lidx(L)].store(((cap < 0 ? 0 : cap) << 1) | (pencil ? 1 : 0));
+  ++g_tune_gen;
+}
+void clear_tuned() {
+  for (int c = 0; c < kcCount; ++c)
+    for (int i = 0; i < kNumL; ++i) g_tuned[c][i].store(0);
+  ++g_tune_gen;
 }
 
 int prof_begin(int cls, cudaStream_t s) {
@@ -271,7 +284,7 @@ struct EngineBase {
   virtual rd_status batch_enqueue(const double*, double, double, cudaStream_t) = 0;
   virtual rd_status batch_finish(double*, double*) = 0;
   virtual void batch_prepare(const double*, double, double) = 0;
-  virtual rd_status autotune(int, int*, int) = 0;
+  virtual rd_status autotune(int, int*, int*, int) = 0;
   virtual bool warm() const = 0;
 };
 
@@ -309,6 +322,7 @@ struct Engine : EngineBase {
   // node over the iteration body (built on first use, reused by every solve)
   cudaGraph_t pcg_graph = nullptr;
   cudaGraphExec_t pcg_exec = nullptr;
+  int pcg_gen = 0;   // autotuner generation the graph was captured under
   bool graph_failed = false;
   int host_solves = 0;
   cudaStream_t cap_stream = nullptr;    // internal stream used only for capture
@@ -730,7 +744,16 @@ struct Engine : EngineBase {
     if (capturing) return pcg_captured();
     const bool profiling = prof_active();
     if (!profiling && !graph_failed && host_solves >= 2) {
-      if (!pcg_exec && !build_pcg_graph()) graph_failed = true;
+      if (pcg_exec && pcg_gen != g_tune_gen.load()) {
+        cudaGraphExecDestroy(pcg_exec);
+        cudaGraphDestroy(pcg_graph);
+        pcg_exec = nullptr;
+        pcg_graph = nullptr;
+      }
+      if (!pcg_exec) {
+        pcg_gen = g_tune_gen.load();
+        if (!build_pcg_graph()) graph_failed = true;
+      }
       if (pcg_exec) {
         if ((e = cudaGraphLaunch(pcg_exec, stream)) != cudaSuccess) return cuda_fail(e, "pcg graph launch");
         ++last_graph_solves;
@@ -1272,27 +1295,34 @@ struct Engine : EngineBase {
   // candidate persistent-grid size (multiples of the SM count) and keeps,
   // per kernel class, the fastest.  The choices apply to every later launch
   // in the process.
-  rd_status autotune(int reps, int* caps_out, int ncls) override {
+  rd_status autotune(int reps, int* caps_out, int* pencil_out, int ncls) override {
     if (!have_tissue) return fail(RD_ERR_STATE, "rd_set_tissue is required");
     int dev = 0, sms = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int kClasses[] = {kcOpStrided, kcPcgOpx, kcDhtPlain, kcDhtSym, kcDhtUpdate};
-    std::vector<int> cands = {0};   // 0: all resident blocks
-    for (int m = 1; m <= 8; ++m) cands.push_back(m * sms);
+    // candidates: tile shape (TMA tiles or pencil groups) x persistent grid
+    // size (all resident blocks, or 1..8 blocks per SM)
+    std::vector<std::pair<int, bool>> cands;
+    for (int v = 0; v < 2; ++v) {
+      cands.push_back({0, v == 1});
+      for (int m = 1; m <= 8; ++m) cands.push_back({m * sms, v == 1});
+    }
     double best[kcCount];
-    int best_cap[kcCount];
+    std::pair<int, bool> choice[kcCount];
     for (int c = 0; c < kcCount; ++c) {
       best[c] = 1e300;
-      best_cap[c] = tuned_cap(c);
+      choice[c] = {tuned_cap(c, g.n[2]), tuned_pencil(c, g.n[2])};
     }
+    auto set_all = [&](int c, std::pair<int, bool> v) {
+      for (int a = 0; a < 3; ++a) set_tuned(c, g.n[a], v.first, v.second);
+    };
     cudaError_t e;
     hprm->k_f = (hprm->k_f > 0.0) ? hprm->k_f : 0.05;
     if ((e = upload_params()) != cudaSuccess) return cuda_fail(e, "upload params");
-    // a smooth right-hand side: f = A kappa1
-    if ((e = apply3(f[F_KAPPA1], f[F_R], 1.0, 1)) != cudaSuccess) return cuda_fail(e, "tune rhs");
-    for (int cap : cands) {
-      for (int c : kClasses) set_tuned_cap(c, cap);
+    for (const auto& cand : cands) {
+      for (int c : kClasses) set_all(c, cand);
+      // a smooth right-hand side: f = A kappa1
       if ((e = apply3(f[F_KAPPA1], f[F_R], 1.0, 1)) != cudaSuccess) return cuda_fail(e, "tune rhs");
       if ((e = enqueue_setup(0)) != cudaSuccess) return cuda_fail(e, "tune setup");
       if ((e = enqueue_iteration(0)) != cudaSuccess) return cuda_fail(e, "tune warm");
@@ -1309,11 +1339,14 @@ struct Engine : EngineBase {
       for (int c : kClasses)
         if (cnt[c] > 0 && ms[c] / cnt[c] < best[c]) {
           best[c] = ms[c] / cnt[c];
-          best_cap[c] = cap;
+          choice[c] = cand;
         }
     }
-    for (int c : kClasses) set_tuned_cap(c, best_cap[c]);
-    for (int c = 0; c < ncls && caps_out; ++c) caps_out[c] = tuned_cap(c);
+    for (int c : kClasses) set_all(c, choice[c]);
+    for (int c = 0; c < ncls; ++c) {
+      if (caps_out) caps_out[c] = tuned_cap(c, g.n[2]);
+      if (pencil_out) pencil_out[c] = tuned_pencil(c, g.n[2]) ? 1 : 0;
+    }
     // leave the PCG state clean for the next solve
     if ((e = cudaMemsetAsync(&st->total_it, 0, 2 * sizeof(int), stream)) != cudaSuccess) return cuda_fail(e, "reset");
     if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return cuda_fail(e, "sync");
@@ -1763,6 +1796,7 @@ namespace {
 // contexts is unchanged.
 struct BatchGraph {
   std::vector<rd_ctx*> ctxs;
+  int gen = 0;   // autotuner generation the graph was captured under
   cudaGraphExec_t exec = nullptr;
   cudaStream_t origin = nullptr;
   std::vector<cudaStream_t> branch;
@@ -1825,12 +1859,13 @@ rd_status rd_batch_gradient(rd_ctx* const* ctxs, int count, const double* const*
     if (cudaStreamSynchronize(e->stream) != cudaSuccess) return RD_ERR_CUDA;
   }
   std::lock_guard<std::mutex> lk(g_batch_mu);
-  const bool same = (int)g_batch.ctxs.size() == count && g_batch.exec &&
+  const bool same = (int)g_batch.ctxs.size() == count && g_batch.exec && g_batch.gen == rd::g_tune_gen.load() &&
                     std::equal(g_batch.ctxs.begin(), g_batch.ctxs.end(), ctxs);
   for (int i = 0; i < count; ++i) ctxs[i]->e->batch_prepare(p[i], k_f[i], rho_f[i]);
   if (!same) {
     g_batch.clear();
     BatchGraph& b = g_batch;
+    b.gen = rd::g_tune_gen.load();
     b.ctxs.assign(ctxs, ctxs + count);
     cudaError_t ce = cudaStreamCreateWithFlags(&b.origin, cudaStreamNonBlocking);
     b.branch.resize(count, nullptr);
@@ -1904,13 +1939,11 @@ rd_status rd_probe_fma_rate(int prec, double* tflops) {
 int rd_last_pcg_iters(const rd_ctx* c) { return c ? c->e->last_iters : 0; }
 int rd_last_graph_solves(const rd_ctx* c) { return c ? c->e->last_graph_solves : 0; }
 
-void rd_autotune_clear(void) {
-  for (int c = 0; c < rd::kcCount; ++c) rd::set_tuned_cap(c, 0);
-}
+void rd_autotune_clear(void) { rd::clear_tuned(); }
 
-rd_status rd_autotune(rd_ctx* c, int reps, int* caps, int ncaps) {
-  if (!c || reps < 1) return RD_ERR_ARG;
-  return c->e->autotune(reps, caps, ncaps);
+rd_status rd_autotune(rd_ctx* c, int reps, int* caps, int* pencil, int ncaps) {
+  if (!c || reps < 1 || ncaps < 0) return RD_ERR_ARG;
+  return c->e->autotune(reps, caps, pencil, ncaps < rd::kcCount ? ncaps : rd::kcCount);
 }
 int rd_last_pcg_solves(const rd_ctx* c) { return c ? c->e->last_solves : 0; }
 

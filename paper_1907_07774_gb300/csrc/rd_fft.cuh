@@ -169,9 +169,16 @@ __device__ __forceinline__ cpx<T> ldtw(const cpx<T>* p) {
   }
 }
 
-// Twiddle load from a shared-memory copy of the table.  The load is
-// volatile so that the compiler re-reads it at each use instead of keeping
-// every twiddle of a persistent loop live in registers.
+// Where a transform reads its twiddles from (template argument TW):
+//   kTwLdg    global memory through the read-only path (__ldg);
+//   kTwShared a shared-memory copy of the table, volatile loads;
+//   kTwGlobal global memory through L1, volatile loads.
+// The volatile forms make the compiler re-read a twiddle at each use instead
+// of keeping every twiddle of a persistent loop live in registers (230
+// registers instead of 96).  Kernels whose occupancy is limited by shared
+// memory use kTwGlobal and keep the 4 KB table out of shared memory.
+constexpr int kTwLdg = 0, kTwShared = 1, kTwGlobal = 2;
+
 template <typename T>
 __device__ __forceinline__ cpx<T> ldtw_shared(const cpx<T>* p) {
   const uint32_t a = static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -184,16 +191,28 @@ __device__ __forceinline__ cpx<T> ldtw_shared(const cpx<T>* p) {
   return v;
 }
 
-template <bool SH, typename T>
+template <typename T>
+__device__ __forceinline__ cpx<T> ldtw_global(const cpx<T>* p) {
+  cpx<T> v;
+  if constexpr (sizeof(T) == 4) {
+    asm volatile("ld.global.nc.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
+  } else {
+    asm volatile("ld.global.nc.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "l"(p));
+  }
+  return v;
+}
+
+template <int TW, typename T>
 __device__ __forceinline__ cpx<T> ldtw_any(const cpx<T>* p) {
-  if constexpr (SH) return ldtw_shared(p);
+  if constexpr (TW == kTwShared) return ldtw_shared(p);
+  else if constexpr (TW == kTwGlobal) return ldtw_global(p);
   else return ldtw(p);
 }
 
 // Twiddle tables (host-computed in FP64, stored in global memory per L):
 //   twA[k1 * TH + t]          = exp(-2 pi i t k1 / L)
 //   twB[(m * TH + n2) * TH + j] = exp(+2 pi i n2 (j + TH m) / L)
-template <typename T, int L, int S, bool SH = false>
+template <typename T, int L, int S, int SH = kTwLdg>
 __device__ __forceinline__ void fft_ab(cpx<T>* v, cpx<T>* sm, int t, const cpx<T>* __restrict__ twA) {
   using Sh = Shape<L>;
   constexpr int R = Sh::R, TH = Sh::TH, PAD = Sh::PAD;
@@ -215,7 +234,7 @@ __device__ __forceinline__ void fft_ab(cpx<T>* v, cpx<T>* sm, int t, const cpx<T
   for (int m = 0; m < R / TH; ++m) Dft<T, TH, S>::run(v + m * TH);
 }
 
-template <typename T, int L, int S, bool SH = false>
+template <typename T, int L, int S, int SH = kTwLdg>
 __device__ __forceinline__ void fft_ba(cpx<T>* u, cpx<T>* sm, int j, const cpx<T>* __restrict__ twB) {
   using Sh = Shape<L>;
   constexpr int R = Sh::R, TH = Sh::TH, PAD = Sh::PAD;

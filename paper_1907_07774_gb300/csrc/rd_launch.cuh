@@ -19,10 +19,16 @@ enum KClass {
 // stream; prof_begin returns a token for prof_end (-1 when off).
 int prof_begin(int cls, cudaStream_t s);
 bool prof_active();
-// Grid-size choices made by the autotuner, per kernel class (0: none, the
-// launcher then uses every block that fits on the device).
-int tuned_cap(int cls);
-void set_tuned_cap(int cls, int cap);
+// Choices made by the autotuner, per kernel class and pencil length L:
+// the persistent grid size (0: none, the launcher then uses every block that
+// fits on the device) and the tile shape (false: the TMA tile kernel, i.e.
+// 64-byte column tiles or whole-row tiles staged in shared memory; true: the
+// pencil kernel, i.e. 256-thread blocks of TH-lane pencil groups with direct
+// loads and stores).
+int tuned_cap(int cls, int L);
+bool tuned_pencil(int cls, int L);
+void set_tuned(int cls, int L, int cap, bool pencil);
+void clear_tuned();
 // Tensor map for TMA tiles of a strided pass: box {64 B of i2, L along the
 // axis}, 64-byte swizzle.  Cached per (pointer, grid, element size, axis);
 // false if the map cannot be made (the caller then uses the direct kernels).

@@ -51,10 +51,10 @@ constexpr size_t pencil_smem() {
 
 template <typename K, typename A>
 cudaError_t launch_pencil(K kern, size_t smem, long long groups_needed, const A& a, cudaStream_t s,
-                          int cls = kcOther) {
+                          int cls = kcOther, int L = 0) {
   const void* fn = reinterpret_cast<const void*>(kern);
   int grid = grid_for(fn, smem, groups_needed);
-  const int tc = tuned_cap(cls);
+  const int tc = tuned_cap(cls, L);
   if (tc > 0 && tc < grid) grid = tc;
   const int tok = prof_begin(cls, s);
   kern<<<grid, kThreads, smem, s>>>(a);
@@ -86,7 +86,8 @@ inline bool tma_fits(const Geom& g) {
 inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
 
 template <typename K, typename A>
-cudaError_t launch_tma(K kern, size_t smem, int threads, long long tiles, const A& a, cudaStream_t s, int cls) {
+cudaError_t launch_tma(K kern, size_t smem, int threads, long long tiles, const A& a, cudaStream_t s, int cls,
+                       int L) {
   const void* fn = reinterpret_cast<const void*>(kern);
   static std::mutex mu;
   static std::unordered_map<const void*, int> cache;
@@ -105,7 +106,7 @@ cudaError_t launch_tma(K kern, size_t smem, int threads, long long tiles, const 
       cap = it->second;
     }
   }
-  const int tc = tuned_cap(cls);
+  const int tc = tuned_cap(cls, L);
   if (tc > 0 && tc < cap) cap = tc;
   const int grid = (int)(tiles < cap ? tiles : cap);
   const int tok = prof_begin(cls, s);
@@ -120,7 +121,8 @@ template <typename T>
 cudaError_t Launch<T>::op(int L, const OpArgs<T>& a, cudaStream_t s) {
   using namespace detail;
   const long long npairs = a.g.nn / L / 2;
-  if (a.axis == 2 && a.a_self == 0 && !a.acc_in && !a.reduce && a.out && a.fin.st && aligned16(a.u) &&
+  if (a.axis == 2 && !tuned_pencil(kcOpContig, L) && a.a_self == 0 && !a.acc_in && !a.reduce && a.out && a.fin.st &&
+      aligned16(a.u) &&
       aligned16(a.kappa) && aligned16(a.out)) {
     RD_DISPATCH_L(L, {
       using TS = TmaRowShape<T, LL>;
@@ -137,13 +139,14 @@ cudaError_t Launch<T>::op(int L, const OpArgs<T>& a, cudaStream_t s) {
           t.twB = a.twB;
           t.prm = a.prm;
           t.st = a.fin.st;
-          return launch_tma(k_op_row_tma<T, LL>, TS::OPROW_SMEM, TS::THREADS, rows / TS::ROWS, t, s, kcOpContig);
+          return launch_tma(k_op_row_tma<T, LL>, TS::OPROW_SMEM, TS::THREADS, rows / TS::ROWS, t, s, kcOpContig, LL);
         }
       }
       break;
     })
   }
-  if (a.axis != 2 && a.a_self == 0 && a.acc_in == a.out && a.out && tma_fits<T>(a.g) && aligned16(a.u) &&
+  if (a.axis != 2 && !tuned_pencil(kcOpStrided, L) && a.a_self == 0 && a.acc_in == a.out && a.out &&
+      tma_fits<T>(a.g) && aligned16(a.u) &&
       aligned16(a.kappa) && aligned16(a.out)) {
     RD_DISPATCH_L(L, {
       using TS = TmaShape<T, LL>;
@@ -167,11 +170,11 @@ cudaError_t Launch<T>::op(int L, const OpArgs<T>& a, cudaStream_t s) {
           const long long tiles = (long long)(a.g.n[2] / TS::W) * (a.axis == 1 ? a.g.n[0] : a.g.n[1]);
           if constexpr (sizeof(T) == 4) {
             if (a.axis == 1)
-              return launch_tma(k_op_tma_red<T, LL, 1>, TS::OPR_SMEM, TS::THREADS, tiles, t, s, kcOpStrided);
-            return launch_tma(k_op_tma_red<T, LL, 0>, TS::OPR_SMEM, TS::THREADS, tiles, t, s, kcOpStrided);
+              return launch_tma(k_op_tma_red<T, LL, 1>, TS::OPR_SMEM, TS::THREADS, tiles, t, s, kcOpStrided, LL);
+            return launch_tma(k_op_tma_red<T, LL, 0>, TS::OPR_SMEM, TS::THREADS, tiles, t, s, kcOpStrided, LL);
           } else {
-            if (a.axis == 1) return launch_tma(k_op_tma<T, LL, 1>, TS::OP_SMEM, TS::THREADS, tiles, t, s, kcOpStrided);
-            return launch_tma(k_op_tma<T, LL, 0>, TS::OP_SMEM, TS::THREADS, tiles, t, s, kcOpStrided);
+            if (a.axis == 1) return launch_tma(k_op_tma<T, LL, 1>, TS::OP_SMEM, TS::THREADS, tiles, t, s, kcOpStrided, LL);
+            return launch_tma(k_op_tma<T, LL, 0>, TS::OP_SMEM, TS::THREADS, tiles, t, s, kcOpStrided, LL);
           }
         }
       }
@@ -181,8 +184,8 @@ cudaError_t Launch<T>::op(int L, const OpArgs<T>& a, cudaStream_t s) {
   RD_DISPATCH_L(L, {
     constexpr size_t sm = pencil_smem<T, LL>();
     const long long blocks = (npairs + Shape<LL>::G - 1) / Shape<LL>::G;
-    if (a.axis == 2) return launch_pencil(k_op<T, LL, true>, sm, blocks, a, s, kcOpContig);
-    return launch_pencil(k_op<T, LL, false>, sm, blocks, a, s, kcOpStrided);
+    if (a.axis == 2) return launch_pencil(k_op<T, LL, true>, sm, blocks, a, s, kcOpContig, LL);
+    return launch_pencil(k_op<T, LL, false>, sm, blocks, a, s, kcOpStrided, LL);
   })
 }
 
@@ -190,7 +193,8 @@ template <typename T>
 cudaError_t Launch<T>::dht(int L, int mode, const DhtArgs<T>& a, cudaStream_t s) {
   using namespace detail;
   const long long npairs = a.g.nn / L / 2;
-  if (a.axis == 2 && (mode == kDhtSetup || mode == kDhtUpdate)) {
+  if (a.axis == 2 && (mode == kDhtSetup || mode == kDhtUpdate) &&
+      !tuned_pencil(mode == kDhtSetup ? kcDhtSetup : kcDhtUpdate, L)) {
     const void* rr = (mode == kDhtSetup) ? (const void*)a.in : (const void*)a.r;
     const bool al = aligned16(rr) && aligned16(a.out) &&
                     (mode == kDhtSetup || (aligned16(a.x) && aligned16(a.p) && aligned16(a.q)));
@@ -218,15 +222,16 @@ cudaError_t Launch<T>::dht(int L, int mode, const DhtArgs<T>& a, cudaStream_t s)
             t.fin = a.fin;
             const long long tiles = rows / TS::ROWS;
             if (mode == kDhtUpdate)
-              return launch_tma(k_dht_row_tma<T, LL, kDhtUpdate>, TS::UPD_SMEM, TS::THREADS, tiles, t, s, kcDhtUpdate);
-            return launch_tma(k_dht_row_tma<T, LL, kDhtSetup>, TS::SETUP_SMEM, TS::THREADS, tiles, t, s, kcDhtSetup);
+              return launch_tma(k_dht_row_tma<T, LL, kDhtUpdate>, TS::UPD_SMEM, TS::THREADS, tiles, t, s, kcDhtUpdate, LL);
+            return launch_tma(k_dht_row_tma<T, LL, kDhtSetup>, TS::SETUP_SMEM, TS::THREADS, tiles, t, s, kcDhtSetup, LL);
           }
         }
         break;
       })
     }
   }
-  if (a.axis != 2 && (mode == kDhtPlain || mode == kDhtSym) && tma_fits<T>(a.g) && aligned16(a.in) &&
+  if (a.axis != 2 && (mode == kDhtPlain || mode == kDhtSym) && !tuned_pencil(mode == kDhtSym ? kcDhtSym : kcDhtPlain, L) &&
+      tma_fits<T>(a.g) && aligned16(a.in) &&
       aligned16(a.out)) {
     RD_DISPATCH_L(L, {
       using TS = TmaShape<T, LL>;
@@ -244,11 +249,11 @@ cudaError_t Launch<T>::dht(int L, int mode, const DhtArgs<T>& a, cudaStream_t s)
           const long long tiles = (long long)(a.g.n[2] / TS::W) * (a.axis == 1 ? a.g.n[0] : a.g.n[1]);
           const int cls = (mode == kDhtSym) ? kcDhtSym : kcDhtPlain;
           if (mode == kDhtSym) {
-            if (a.axis == 1) return launch_tma(k_dht_tma<T, LL, 1, kDhtSym>, TS::DHT_SMEM, TS::THREADS, tiles, t, s, cls);
-            return launch_tma(k_dht_tma<T, LL, 0, kDhtSym>, TS::DHT_SMEM, TS::THREADS, tiles, t, s, cls);
+            if (a.axis == 1) return launch_tma(k_dht_tma<T, LL, 1, kDhtSym>, TS::DHT_SMEM, TS::THREADS, tiles, t, s, cls, LL);
+            return launch_tma(k_dht_tma<T, LL, 0, kDhtSym>, TS::DHT_SMEM, TS::THREADS, tiles, t, s, cls, LL);
           }
-          if (a.axis == 1) return launch_tma(k_dht_tma<T, LL, 1, kDhtPlain>, TS::DHT_SMEM, TS::THREADS, tiles, t, s, cls);
-          return launch_tma(k_dht_tma<T, LL, 0, kDhtPlain>, TS::DHT_SMEM, TS::THREADS, tiles, t, s, cls);
+          if (a.axis == 1) return launch_tma(k_dht_tma<T, LL, 1, kDhtPlain>, TS::DHT_SMEM, TS::THREADS, tiles, t, s, cls, LL);
+          return launch_tma(k_dht_tma<T, LL, 0, kDhtPlain>, TS::DHT_SMEM, TS::THREADS, tiles, t, s, cls, LL);
         }
       }
       break;
@@ -259,14 +264,14 @@ cudaError_t Launch<T>::dht(int L, int mode, const DhtArgs<T>& a, cudaStream_t s)
     const long long blocks = (npairs + Shape<LL>::G - 1) / Shape<LL>::G;
     switch (mode) {
       case kDhtPlain:
-        if (a.axis == 2) return launch_pencil(k_dht<T, LL, true, kDhtPlain>, sm, blocks, a, s, kcDhtPlain);
-        return launch_pencil(k_dht<T, LL, false, kDhtPlain>, sm, blocks, a, s, kcDhtPlain);
+        if (a.axis == 2) return launch_pencil(k_dht<T, LL, true, kDhtPlain>, sm, blocks, a, s, kcDhtPlain, LL);
+        return launch_pencil(k_dht<T, LL, false, kDhtPlain>, sm, blocks, a, s, kcDhtPlain, LL);
       case kDhtSetup:
-        return launch_pencil(k_dht<T, LL, true, kDhtSetup>, sm, blocks, a, s, kcDhtSetup);
+        return launch_pencil(k_dht<T, LL, true, kDhtSetup>, sm, blocks, a, s, kcDhtSetup, LL);
       case kDhtUpdate:
-        return launch_pencil(k_dht<T, LL, true, kDhtUpdate>, sm, blocks, a, s, kcDhtUpdate);
+        return launch_pencil(k_dht<T, LL, true, kDhtUpdate>, sm, blocks, a, s, kcDhtUpdate, LL);
       case kDhtSym:
-        return launch_pencil(k_dht<T, LL, false, kDhtSym>, sm, blocks, a, s, kcDhtSym);
+        return launch_pencil(k_dht<T, LL, false, kDhtSym>, sm, blocks, a, s, kcDhtSym, LL);
       default:
         return cudaErrorInvalidValue;
     }
@@ -277,7 +282,7 @@ template <typename T>
 cudaError_t Launch<T>::pcg_opx(int L, const PcgOpxArgs<T>& a, cudaStream_t s) {
   using namespace detail;
   const long long npairs = a.g.nn / L / 2;
-  if (aligned16(a.w) && aligned16(a.p) && aligned16(a.q) && aligned16(a.kappa)) {
+  if (!tuned_pencil(kcPcgOpx, L) && aligned16(a.w) && aligned16(a.p) && aligned16(a.q) && aligned16(a.kappa)) {
     RD_DISPATCH_L(L, {
       using TS = TmaRowShape<T, LL>;
       if constexpr (TS::OK) {
@@ -294,7 +299,7 @@ cudaError_t Launch<T>::pcg_opx(int L, const PcgOpxArgs<T>& a, cudaStream_t s) {
           t.st = a.st;
           t.fin = a.fin;
           t.rowact = a.rowact;
-          return launch_tma(k_pcg_opx_tma<T, LL>, TS::OPX_SMEM, TS::THREADS, rows / TS::ROWS, t, s, kcPcgOpx);
+          return launch_tma(k_pcg_opx_tma<T, LL>, TS::OPX_SMEM, TS::THREADS, rows / TS::ROWS, t, s, kcPcgOpx, LL);
         }
       }
       break;
@@ -303,7 +308,7 @@ cudaError_t Launch<T>::pcg_opx(int L, const PcgOpxArgs<T>& a, cudaStream_t s) {
   RD_DISPATCH_L(L, {
     constexpr size_t sm = pencil_smem<T, LL>();
     const long long blocks = (npairs + Shape<LL>::G - 1) / Shape<LL>::G;
-    return launch_pencil(k_pcg_opx<T, LL>, sm, blocks, a, s, kcPcgOpx);
+    return launch_pencil(k_pcg_opx<T, LL>, sm, blocks, a, s, kcPcgOpx, LL);
   })
 }
 
@@ -311,7 +316,8 @@ template <typename T>
 cudaError_t Launch<T>::grad(int L, const GradArgs<T>& a, cudaStream_t s) {
   using namespace detail;
   const long long npairs = a.g.nn / L / 2;
-  if (a.axis != 2 && !a.q && tma_fits<T>(a.g) && aligned16(a.u0) && (!a.u1 || aligned16(a.u1)) && aligned16(a.w) &&
+  if (a.axis != 2 && !tuned_pencil(kcGrad, L) && !a.q && tma_fits<T>(a.g) && aligned16(a.u0) &&
+      (!a.u1 || aligned16(a.u1)) && aligned16(a.w) &&
       aligned16(a.kappa)) {
     RD_DISPATCH_L(L, {
       using TS = TmaShape<T, LL>;
@@ -329,8 +335,8 @@ cudaError_t Launch<T>::grad(int L, const GradArgs<T>& a, cudaStream_t s) {
           t.tiles = a.tiles;
           t.ntiles_act = a.ntiles_act;
           const long long tiles = (long long)(a.g.n[2] / TS::W) * (a.axis == 1 ? a.g.n[0] : a.g.n[1]);
-          if (a.axis == 1) return launch_tma(k_grad_tma<T, LL, 1>, TS::GRAD_SMEM, TS::THREADS, tiles, t, s, kcGrad);
-          return launch_tma(k_grad_tma<T, LL, 0>, TS::GRAD_SMEM, TS::THREADS, tiles, t, s, kcGrad);
+          if (a.axis == 1) return launch_tma(k_grad_tma<T, LL, 1>, TS::GRAD_SMEM, TS::THREADS, tiles, t, s, kcGrad, LL);
+          return launch_tma(k_grad_tma<T, LL, 0>, TS::GRAD_SMEM, TS::THREADS, tiles, t, s, kcGrad, LL);
         }
       }
       break;
@@ -339,8 +345,8 @@ cudaError_t Launch<T>::grad(int L, const GradArgs<T>& a, cudaStream_t s) {
   RD_DISPATCH_L(L, {
     constexpr size_t sm = pencil_smem<T, LL>();
     const long long blocks = (npairs + Shape<LL>::G - 1) / Shape<LL>::G;
-    if (a.axis == 2) return launch_pencil(k_grad<T, LL, true>, sm, blocks, a, s, kcGrad);
-    return launch_pencil(k_grad<T, LL, false>, sm, blocks, a, s, kcGrad);
+    if (a.axis == 2) return launch_pencil(k_grad<T, LL, true>, sm, blocks, a, s, kcGrad, LL);
+    return launch_pencil(k_grad<T, LL, false>, sm, blocks, a, s, kcGrad, LL);
   })
 }
 

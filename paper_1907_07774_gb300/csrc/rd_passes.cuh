@@ -81,12 +81,18 @@ __device__ __forceinline__ cpx<T> times_ik(cpx<T> v, int k) {
   return {-T(k) * v.y, T(k) * v.x};
 }
 
-// 1/x for x >= 1 in the working precision.  FP32: the round-to-nearest
-// reciprocal intrinsic.
+// 1/x for x >= 1 in the working precision.  FP32: the approximate PTX
+// reciprocal (a relative error of about 2^-23; it only enters the
+// preconditioner symbol, which changes how fast PCG converges, not what it
+// converges to).
 // FP64: an FP32 reciprocal refined by two Newton-Raphson steps
 // r <- r (2 - x r) (each step squares the relative error, 2^-24 -> 2^-96),
 // which avoids the much slower FP64 division on this part.
-__device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ float recip(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
 __device__ __forceinline__ double recip(double x) {
   double r = double(1.0f / float(x));
   r = r * (2.0 - x * r);

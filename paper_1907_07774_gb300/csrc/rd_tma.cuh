@@ -251,10 +251,10 @@ __global__ void __launch_bounds__(TmaShape<T, L>::THREADS) k_op_tma(const __grid
         issue(q_buf, &a.map_q, &qbar, pq, tile);
       }
     }
-    fft_ab<T, L, -1, true>(v, sm, t, twA);
+    fft_ab<T, L, -1, kTwShared>(v, sm, t, twA);
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = times_ik(v[r], kwave<L>(idx_b<L>(r, t)));
-    fft_ba<T, L, +1, true>(v, sm, t, twB);
+    fft_ba<T, L, +1, kTwShared>(v, sm, t, twB);
     ok = mbar_wait(&kbar, i & 1);
     if (__syncthreads_or(!ok)) { bad = true; break; }
     ++pk.done;
@@ -269,10 +269,10 @@ __global__ void __launch_bounds__(TmaShape<T, L>::THREADS) k_op_tma(const __grid
     red += double(loc);
     __syncthreads();   // every kappa value is in registers
     if (threadIdx.x == 0 && more) issue(k_buf, &a.map_k, &kbar, pk, tile_at(j + stride));
-    fft_ab<T, L, -1, true>(v, sm, t, twA);
+    fft_ab<T, L, -1, kTwShared>(v, sm, t, twA);
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = times_ik(v[r], kwave<L>(idx_b<L>(r, t)));
-    fft_ba<T, L, +1, true>(v, sm, t, twB);
+    fft_ba<T, L, +1, kTwShared>(v, sm, t, twB);
     ok = mbar_wait(&qbar, i & 1);
     if (__syncthreads_or(!ok)) { bad = true; break; }
     ++pq.done;
@@ -369,10 +369,10 @@ __global__ void __launch_bounds__(TmaShape<T, L>::THREADS) k_op_tma_red(const __
     for (int r = 0; r < R; ++r) v[r] = *tile_pair<T>(u_buf, idx_a<L>(r, t), g);
     __syncthreads();   // every u value is in registers
     if (threadIdx.x == 0 && more) issue(u_buf, &a.map_u, &ubar, pu, tile_at(j + stride));
-    fft_ab<T, L, -1, true>(v, sm, t, twA);
+    fft_ab<T, L, -1, kTwShared>(v, sm, t, twA);
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = times_ik(v[r], kwave<L>(idx_b<L>(r, t)));
-    fft_ba<T, L, +1, true>(v, sm, t, twB);
+    fft_ba<T, L, +1, kTwShared>(v, sm, t, twB);
     ok = mbar_wait(&kbar, i & 1);
     if (__syncthreads_or(!ok)) { bad = true; break; }
     ++pk.done;
@@ -386,10 +386,10 @@ __global__ void __launch_bounds__(TmaShape<T, L>::THREADS) k_op_tma_red(const __
     }
     red += double(loc);
     __syncthreads();   // every kappa value is in registers: k_buf is free
-    fft_ab<T, L, -1, true>(v, sm, t, twA);
+    fft_ab<T, L, -1, kTwShared>(v, sm, t, twA);
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = times_ik(v[r], kwave<L>(idx_b<L>(r, t)));
-    fft_ba<T, L, +1, true>(v, sm, t, twB);
+    fft_ba<T, L, +1, kTwShared>(v, sm, t, twB);
 #pragma unroll
     for (int r = 0; r < R; ++r) *tile_pair<T>(k_buf, idx_a<L>(r, t), g) = {coef * v[r].x, coef * v[r].y};
     fence_proxy_async();
@@ -489,8 +489,8 @@ __global__ void __launch_bounds__(TmaShape<T, L>::THREADS, (MODE == kDhtSym && s
       bulk_wait_read0();
       issue(tile + stride, b ^ 1);
     }
-    fft_ab<T, L, -1, true>(v, sm, t, twA);
-    if (MODE != kDhtSym) hartley_combine<T, L, true>(v, t);
+    fft_ab<T, L, -1, kTwShared>(v, sm, t, twA);
+    if (MODE != kDhtSym) hartley_combine<T, L, kTwShared>(v, t);
     T loc = T(0);
     if (MODE == kDhtSym) {
       int c0, c1, c2;
@@ -500,7 +500,7 @@ __global__ void __launch_bounds__(TmaShape<T, L>::THREADS, (MODE == kDhtSym && s
       const T base_a = T(k1 * k1 + k2a * k2a);
       const T base_b = T(k1 * k1 + k2b * k2b);
       loc = sym_apply<T, L>(v, t, base_a, base_b, T(symc), T(inv_nn));
-      fft_ba<T, L, +1, true>(v, sm, t, twB);
+      fft_ba<T, L, +1, kTwShared>(v, sm, t, twB);
 #pragma unroll
       for (int r = 0; r < R; ++r) *tile_pair<T>(st_buf(b), idx_a<L>(r, t), g) = v[r];
     } else {
@@ -620,10 +620,10 @@ __global__ void __launch_bounds__(TmaShape<T, L>::THREADS) k_grad_tma(const __gr
       issue(a_buf, &a.map_k, &abar, pa, tile);
       if (two && more) issue(b_buf, &a.map_u1, &bbar, pb, tile_at(j + stride));
     }
-    fft_ab<T, L, -1, true>(du, sm, t, twA);
+    fft_ab<T, L, -1, kTwShared>(du, sm, t, twA);
 #pragma unroll
     for (int r = 0; r < R; ++r) du[r] = times_ik(du[r], kwave<L>(idx_b<L>(r, t)));
-    fft_ba<T, L, +1, true>(du, sm, t, twB);
+    fft_ba<T, L, +1, kTwShared>(du, sm, t, twB);
     ok = mbar_wait(&cbar, i & 1);
     if (__syncthreads_or(!ok)) { bad = true; break; }
     ++pc.done;
@@ -632,10 +632,10 @@ __global__ void __launch_bounds__(TmaShape<T, L>::THREADS) k_grad_tma(const __gr
     for (int r = 0; r < R; ++r) dw[r] = *tile_pair<T>(c_buf, idx_a<L>(r, t), g);
     __syncthreads();   // every w value is in registers
     if (threadIdx.x == 0 && more) issue(c_buf, &a.map_w, &cbar, pc, tile_at(j + stride));
-    fft_ab<T, L, -1, true>(dw, sm, t, twA);
+    fft_ab<T, L, -1, kTwShared>(dw, sm, t, twA);
 #pragma unroll
     for (int r = 0; r < R; ++r) dw[r] = times_ik(dw[r], kwave<L>(idx_b<L>(r, t)));
-    fft_ba<T, L, +1, true>(dw, sm, t, twB);
+    fft_ba<T, L, +1, kTwShared>(dw, sm, t, twB);
     ok = mbar_wait(&abar, 1);
     if (__syncthreads_or(!ok)) { bad = true; break; }
     ++pa.done;
@@ -683,7 +683,7 @@ struct TmaRowShape {
   static constexpr int XSTRIDE = R * (TH + 1);
   static constexpr int XBYTES = PAIRS * XSTRIDE * int(sizeof(cpx<T>));
   static constexpr bool OK = (THREADS >= 32) && (THREADS % 32 == 0);
-  static constexpr int TWBYTES = 2 * L * int(sizeof(cpx<T>));
+  static constexpr int TWBYTES = 0;   // twiddles are read from global memory (kTwGlobal)
   static constexpr size_t OPX_SMEM = 3 * size_t(TILE_BYTES) + XBYTES + TWBYTES + 128;
   static constexpr size_t OPROW_SMEM = 2 * size_t(TILE_BYTES) + XBYTES + TWBYTES + 128;
   static constexpr size_t UPD_SMEM = 8 * size_t(TILE_BYTES) + XBYTES + TWBYTES + 1024;
@@ -739,9 +739,9 @@ __global__ void __launch_bounds__(TmaRowShape<T, L>::THREADS) k_op_row_tma(const
   unsigned char* k_buf = smem + TB;
   cpx<T>* xbuf = reinterpret_cast<cpx<T>*>(smem + 2 * TB);
   cpx<T>* tws = reinterpret_cast<cpx<T>*>(smem + 2 * TB + S::XBYTES);
-  const cpx<T>* twA = tws;
-  const cpx<T>* twB = tws + L;
-  stage_twiddles<T, L>(tws, a.twA, a.twB);
+  const cpx<T>* twA = a.twA;   // read through L1 (kTwGlobal)
+  const cpx<T>* twB = a.twB;
+  (void)tws;
   __shared__ uint64_t ubar, kbar;
   const int g = threadIdx.x / TH, t = threadIdx.x % TH;
   cpx<T>* sm = xbuf + g * S::XSTRIDE;
@@ -782,10 +782,10 @@ __global__ void __launch_bounds__(TmaRowShape<T, L>::THREADS) k_op_row_tma(const
     }
     __syncthreads();   // every u value is in registers
     if (threadIdx.x == 0 && more) issue(u_buf, &a.map_u, &ubar, pu, tile + stride);
-    fft_ab<T, L, -1, true>(v, sm, t, twA);
+    fft_ab<T, L, -1, kTwGlobal>(v, sm, t, twA);
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = times_ik(v[r], kwave<L>(idx_b<L>(r, t)));
-    fft_ba<T, L, +1, true>(v, sm, t, twB);
+    fft_ba<T, L, +1, kTwGlobal>(v, sm, t, twB);
     ok = mbar_wait(&kbar, i & 1);
     if (__syncthreads_or(!ok)) { bad = true; break; }
     ++pk.done;
@@ -797,10 +797,10 @@ __global__ void __launch_bounds__(TmaRowShape<T, L>::THREADS) k_op_row_tma(const
     }
     __syncthreads();   // every kappa value is in registers
     if (threadIdx.x == 0 && more) issue(k_buf, &a.map_k, &kbar, pk, tile + stride);
-    fft_ab<T, L, -1, true>(v, sm, t, twA);
+    fft_ab<T, L, -1, kTwGlobal>(v, sm, t, twA);
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = times_ik(v[r], kwave<L>(idx_b<L>(r, t)));
-    fft_ba<T, L, +1, true>(v, sm, t, twB);
+    fft_ba<T, L, +1, kTwGlobal>(v, sm, t, twB);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const int n = idx_a<L>(r, t);
@@ -854,9 +854,9 @@ __global__ void __launch_bounds__(TmaRowShape<T, L>::THREADS) k_pcg_opx_tma(cons
   unsigned char* p_buf = smem + 2 * TB;
   cpx<T>* xbuf = reinterpret_cast<cpx<T>*>(smem + 3 * TB);
   cpx<T>* tws = reinterpret_cast<cpx<T>*>(smem + 3 * TB + S::XBYTES);
-  const cpx<T>* twA = tws;
-  const cpx<T>* twB = tws + L;
-  stage_twiddles<T, L>(tws, a.twA, a.twB);
+  const cpx<T>* twA = a.twA;   // read through L1 (kTwGlobal)
+  const cpx<T>* twB = a.twB;
+  (void)tws;
   __shared__ uint64_t wbar, kbar, pbar;
   const int g = threadIdx.x / TH, t = threadIdx.x % TH;
   cpx<T>* sm = xbuf + g * S::XSTRIDE;
@@ -913,8 +913,8 @@ __global__ void __launch_bounds__(TmaRowShape<T, L>::THREADS) k_pcg_opx_tma(cons
     }
     __syncthreads();   // every w value is in registers
     if (threadIdx.x == 0 && more) issue(w_buf, &a.map_w, &wbar, pw, tile + stride);
-    fft_ab<T, L, -1, true>(v, sm, t, twA);
-    hartley_combine<T, L, true>(v, t);
+    fft_ab<T, L, -1, kTwGlobal>(v, sm, t, twA);
+    hartley_combine<T, L, kTwGlobal>(v, t);
     if (use_p) {
       ok = mbar_wait(&pbar, i & 1);
       if (__syncthreads_or(!ok)) { bad = true; break; }
@@ -943,10 +943,10 @@ __global__ void __launch_bounds__(TmaRowShape<T, L>::THREADS) k_pcg_opx_tma(cons
     // enough for the instruction cache)
 #pragma unroll 1
     for (int pass = 0; pass < (act ? 2 : 0); ++pass) {
-      fft_ba<T, L, -1, true>(v, sm, t, twB);
+      fft_ba<T, L, -1, kTwGlobal>(v, sm, t, twB);
 #pragma unroll
       for (int r = 0; r < R; ++r) v[r] = times_ik(v[r], kwave<L>(idx_a<L>(r, t)));
-      fft_ab<T, L, +1, true>(v, sm, t, twA);
+      fft_ab<T, L, +1, kTwGlobal>(v, sm, t, twA);
       if (pass == 1) break;
       ok = mbar_wait(&kbar, pk.done & 1);
       if (__syncthreads_or(!ok)) { bad = true; break; }
@@ -1025,9 +1025,9 @@ __global__ void __launch_bounds__(TmaRowShape<T, L>::THREADS) k_dht_row_tma(cons
   auto fld = [&](int b, int f) { return smem + (b * NF + f) * TB; };
   cpx<T>* xbuf = reinterpret_cast<cpx<T>*>(smem + 2 * NF * TB);
   cpx<T>* tws = reinterpret_cast<cpx<T>*>(smem + 2 * NF * TB + S::XBYTES);
-  const cpx<T>* twA = tws;
-  const cpx<T>* twB = tws + L;
-  stage_twiddles<T, L>(tws, a.twA, a.twB);
+  const cpx<T>* twA = a.twA;   // read through L1 (kTwGlobal)
+  const cpx<T>* twB = a.twB;
+  (void)tws;
   __shared__ uint64_t full[2];
   const int g = threadIdx.x / TH, t = threadIdx.x % TH;
   cpx<T>* sm = xbuf + g * S::XSTRIDE;
@@ -1093,8 +1093,8 @@ __global__ void __launch_bounds__(TmaRowShape<T, L>::THREADS) k_dht_row_tma(cons
       bulk_wait_read0();
       issue(tile + stride, b ^ 1);
     }
-    fft_ab<T, L, -1, true>(v, sm, t, twA);
-    hartley_combine<T, L, true>(v, t);
+    fft_ab<T, L, -1, kTwGlobal>(v, sm, t, twA);
+    hartley_combine<T, L, kTwGlobal>(v, t);
     // Hartley values go to the p tile (update) or back into the r tile (setup)
     unsigned char* ob = (MODE == kDhtUpdate) ? fld(b, 2) : fld(b, 0);
     if (MODE != kDhtUpdate) __syncwarp();

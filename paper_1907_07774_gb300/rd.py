@@ -66,7 +66,7 @@ def lib():
         "rd_last_pcg_solves": ([vp], ci),
         "rd_last_graph_solves": ([vp], ci),
         "rd_batch_gradient": ([vp, ci, vp, vp, vp, vp, vp], st),
-        "rd_autotune": ([vp, ci, vp, ci], st),
+        "rd_autotune": ([vp, ci, vp, vp, ci], st),
         "rd_autotune_clear": ([], None),
         "rd_last_error": ([vp], ctypes.c_char_p),
         "rd_destroy": ([vp], None),
@@ -319,12 +319,13 @@ class Context:
         return lib().rd_last_pcg_iters(self.h)
 
     def rd_autotune(self, reps=3):
-        """Tune grid sizes per kernel class on this grid; returns
-        {class: blocks (0 = all resident)}."""
-        n = 16
+        """Tune tile shape and grid size per kernel class on this grid;
+        returns {class: (blocks (0 = all resident), "pencil" | "tma")}."""
+        n = 10
         caps = (ctypes.c_int * n)()
-        self._call(lib().rd_autotune(self.h, int(reps), caps, n))
-        return {lib().rd_profile_class(i).decode(): caps[i] for i in range(10)}
+        pen = (ctypes.c_int * n)()
+        self._call(lib().rd_autotune(self.h, int(reps), caps, pen, n))
+        return {lib().rd_profile_class(i).decode(): (caps[i], "pencil" if pen[i] else "tma") for i in range(n)}
 
     def rd_last_graph_solves(self):
         return lib().rd_last_graph_solves(self.h)

@@ -513,6 +513,7 @@ def test_autotuned_grid_sizes_keep_parity():
     try:
         caps = ctx.rd_autotune(reps=2)
         assert set(caps) >= {"op_axis01", "pcg_opx", "dht_plain", "dht_sym", "dht_update"}
+        assert all(shape in ("tma", "pencil") and blocks >= 0 for blocks, shape in caps.values())
         J, g = ctx.rd_gradient(prob.p, prob.k_f, prob.rho_f)
         assert rel(g, g_or) <= TOL["mixed"] and abs(J - J_or) <= TOL["mixed"] * J_or
     finally:

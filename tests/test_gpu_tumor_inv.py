@@ -42,3 +42,52 @@ def test_tumor_inversion_on_gpu_gives_a_sparse_start_and_lowers_the_misfit():
     assert out.k_f >= 0.0
     fs = [h["f"] for h in out.l2.history]
     assert fs and all(b < a for a, b in zip(fs, fs[1:])), [(h["f"], h["ls"]) for h in out.l2.history]
+
+
+class OracleSolver:
+    """The oracle behind the calls the optimiser makes (rd_forward,
+    rd_adjoint of the last forward, rd_gradient), FP64 on the CPU."""
+
+    def __init__(self, M, d):
+        self.M, self.d = M, d
+        self.np = M.g[0].shape[0]
+        self.last = None
+
+    def rd_forward(self, p, k_f, rho_f):
+        p = np.asarray(p, dtype=np.float64)
+        c1, traj = self.M.forward(p, k_f, rho_f)
+        self.last = (p, k_f, rho_f, c1, traj)
+        return self.M.misfit(c1, self.d, p)
+
+    def rd_adjoint(self):
+        p, k_f, rho_f, c1, traj = self.last
+        a0, g_kf, g_rho = self.M.adjoint(traj, self.M.final_adjoint(c1, self.d), k_f, rho_f)
+        return np.concatenate([-self.M.h3 * self.M.phi_t(a0) + self.M.beta_p * p, [g_kf, g_rho]])
+
+    def rd_gradient(self, p, k_f, rho_f):
+        J = self.rd_forward(p, k_f, rho_f)
+        return J, self.rd_adjoint()
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-8), ("mixed", 2e-4)])
+def test_tumor_inversion_driven_by_gpu_matches_the_same_run_driven_by_the_oracle(prec, tol):
+    """Sec. 2.3 and 3.1: the same l1/l2 optimiser run twice on a 16^3 problem,
+    once on the CUDA context and once on the oracle; the beta search tries
+    the same values and both phases end at the same iterate."""
+    prob = synth.calibration_problem(n=16, nt=4, m=3, sigma=2 * math.pi / 10)
+    M = orc.model_from_problem(prob, rtol=1e-13, maxit=1000, kind="numpy")
+    c_true, _ = M.forward(prob.p_true, prob.k_f_true, prob.rho_f_true)
+    d = synth.labels(c_true, synth.ellipsoid_mask(prob.n), 7)
+    kw = dict(rho_f=prob.rho_f_true, k_f_l2=0.02, beta_steps=4, gist_kw={"maxit": 25, "tau_j": 1e-6},
+              tau_s=0.1, w_large=1.0, w_small=0.0, beta_l2=1e-4, opttol=1e-3, l2_maxit=12)
+    ref = T.tumor_inversion(OracleSolver(M, d), **kw)
+    ctx = R.context_for(prob, prec=prec, pcg_rtol=1e-12 if prec == "fp64" else 1e-6, pcg_maxit=1000)
+    ctx.rd_set_data(d)
+    got = T.tumor_inversion(ctx, **kw)
+    assert [t["beta"] for t in got.l1.tried] == pytest.approx([t["beta"] for t in ref.l1.tried], rel=tol)
+    assert np.linalg.norm(got.l1.p - ref.l1.p) <= tol * np.linalg.norm(ref.l1.p)
+    assert got.l2.iters == ref.l2.iters
+    x_got = np.concatenate([got.p, [got.k_f]])
+    x_ref = np.concatenate([ref.p, [ref.k_f]])
+    assert np.linalg.norm(x_got - x_ref) <= tol * np.linalg.norm(x_ref)
+    assert abs(got.misfit - ref.misfit) <= tol * ref.misfit
