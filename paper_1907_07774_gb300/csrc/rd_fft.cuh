@@ -259,6 +259,14 @@ __device__ __forceinline__ void fft_ba(cpx<T>* u, cpx<T>* sm, int j, const cpx<T
   Dft<T, R, S>::run(u);
 }
 
+// Complex conjugate of R register values: an inverse transform is the
+// forward one between two conjugations (exact: only signs change).
+template <typename T, int R>
+__device__ __forceinline__ void conj_all(cpx<T>* v) {
+#pragma unroll
+  for (int r = 0; r < R; ++r) v[r].y = -v[r].y;
+}
+
 // Index held by register r of lane t in each layout.
 template <int L>
 __device__ __forceinline__ int idx_a(int r, int t) { return Shape<L>::TH * r + t; }

@@ -368,7 +368,16 @@ __global__ void __launch_bounds__(TmaShape<T, L>::THREADS) k_op_tma_red(const __
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = *tile_pair<T>(u_buf, idx_a<L>(r, t), g);
     __syncthreads();   // every u value is in registers
-    if (threadIdx.x == 0 && more) issue(u_buf, &a.map_u, &ubar, pu, tile_at(j + stride));
+    if (threadIdx.x == 0) {
+      if (more) issue(u_buf, &a.map_u, &ubar, pu, tile_at(j + stride));
+      if (i > 0) {
+        // kappa of this tile goes into k_buf once the previous tile's
+        // reduce-add has read it; requested here, two transforms before it
+        // is needed, so that no warp waits for that read at a block barrier
+        bulk_wait_read0();
+        issue(k_buf, &a.map_k, &kbar, pk, tile);
+      }
+    }
     fft_ab<T, L, -1, kTwShared>(v, sm, t, twA);
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = times_ik(v[r], kwave<L>(idx_b<L>(r, t)));
@@ -399,8 +408,6 @@ __global__ void __launch_bounds__(TmaShape<T, L>::THREADS) k_op_tma_red(const __
       tile_coords(a.g, AXIS, S::W, tile, c0, c1, c2);
       tma_reduce_add3(&a.map_q, k_buf, c0, c1, c2);
       bulk_commit();
-      bulk_wait_read0();
-      if (more) issue(k_buf, &a.map_k, &kbar, pk, tile_at(j + stride));
     }
   }
   if (threadIdx.x == 0) bulk_wait0();
@@ -490,7 +497,7 @@ __global__ void __launch_bounds__(TmaShape<T, L>::THREADS, (MODE == kDhtSym && s
       issue(tile + stride, b ^ 1);
     }
     fft_ab<T, L, -1, kTwShared>(v, sm, t, twA);
-    if (MODE != kDhtSym) hartley_combine<T, L, kTwShared>(v, t);
+    if (MODE != kDhtSym) hartley_combine<T, L, true>(v, t);
     T loc = T(0);
     if (MODE == kDhtSym) {
       int c0, c1, c2;
@@ -913,56 +920,68 @@ __global__ void __launch_bounds__(TmaRowShape<T, L>::THREADS) k_pcg_opx_tma(cons
     }
     __syncthreads();   // every w value is in registers
     if (threadIdx.x == 0 && more) issue(w_buf, &a.map_w, &wbar, pw, tile + stride);
-    fft_ab<T, L, -1, kTwGlobal>(v, sm, t, twA);
-    hartley_combine<T, L, kTwGlobal>(v, t);
-    if (use_p) {
-      ok = mbar_wait(&pbar, i & 1);
-      if (__syncthreads_or(!ok)) { bad = true; break; }
-      ++pp.done;
-#pragma unroll
-      for (int r = 0; r < R; ++r) {
-        const int n = idx_b<L>(r, t);
-        v[r].x += beta * *row_elem<T, L>(p_buf, ra, n);
-        v[r].y += beta * *row_elem<T, L>(p_buf, rb, n);
-      }
-      __syncthreads();   // every old p value is in registers
-      if (threadIdx.x == 0 && more) issue(p_buf, &a.map_p, &pbar, pp, tile + stride);
-    }
     constexpr bool KEEP_P = R * int(sizeof(T)) <= 64;
     cpx<T> pv[KEEP_P ? R : 1];
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const int n = idx_b<L>(r, t);
-      if constexpr (KEEP_P) pv[r] = v[r];
-      lpp += v[r].x * v[r].x + v[r].y * v[r].y;
-      prow_a[n] = v[r].x;
-      prow_b[n] = v[r].y;
-    }
-    // d(kappa d p): the two derivative applications share one copy of the
-    // transform code (a loop that is not unrolled keeps the kernel small
-    // enough for the instruction cache)
+    // Five transforms per tile through two copies of the transform code (a
+    // loop that is not unrolled keeps the kernel within the instruction
+    // cache): step 0 is the Hartley pass of w (forward, A -> B); steps 1-4
+    // are d(kappa d p): forward B -> A, i k, inverse A -> B, kappa, forward
+    // B -> A, i k, inverse A -> B.  The inverse A -> B transform is the
+    // forward one between two conjugations.  Row tiles without kappa stop
+    // after step 0 (q = p there).
+    const int nsteps = act ? 5 : 1;
 #pragma unroll 1
-    for (int pass = 0; pass < (act ? 2 : 0); ++pass) {
-      fft_ba<T, L, -1, kTwGlobal>(v, sm, t, twB);
-#pragma unroll
-      for (int r = 0; r < R; ++r) v[r] = times_ik(v[r], kwave<L>(idx_a<L>(r, t)));
-      fft_ab<T, L, +1, kTwGlobal>(v, sm, t, twA);
-      if (pass == 1) break;
-      ok = mbar_wait(&kbar, pk.done & 1);
-      if (__syncthreads_or(!ok)) { bad = true; break; }
-      ++pk.done;
-#pragma unroll
-      for (int r = 0; r < R; ++r) {
-        const int n = idx_b<L>(r, t);
-        const T ka = *row_elem<T, L>(k_buf, ra, n), kb = *row_elem<T, L>(k_buf, rb, n);
-        lk += ka * v[r].x * v[r].x + kb * v[r].y * v[r].y;
-        v[r].x *= ka;
-        v[r].y *= kb;
+    for (int step = 0; step < nsteps; ++step) {
+      if ((step & 1) == 0) {
+        if (step > 0) conj_all<T, R>(v);
+        fft_ab<T, L, -1, kTwGlobal>(v, sm, t, twA);
+        if (step > 0) conj_all<T, R>(v);
+      } else {
+        fft_ba<T, L, -1, kTwGlobal>(v, sm, t, twB);
       }
-      __syncthreads();   // every kappa value is in registers
-      if (threadIdx.x == 0) {
-        const long long kt = next_act(tile + stride);
-        if (kt < ntiles) issue(k_buf, &a.map_k, &kbar, pk, kt);
+      if (step == 0) {
+        hartley_combine<T, L, true>(v, t);
+        if (use_p) {
+          ok = mbar_wait(&pbar, i & 1);
+          if (__syncthreads_or(!ok)) { bad = true; break; }
+          ++pp.done;
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            const int n = idx_b<L>(r, t);
+            v[r].x += beta * *row_elem<T, L>(p_buf, ra, n);
+            v[r].y += beta * *row_elem<T, L>(p_buf, rb, n);
+          }
+          __syncthreads();   // every old p value is in registers
+          if (threadIdx.x == 0 && more) issue(p_buf, &a.map_p, &pbar, pp, tile + stride);
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const int n = idx_b<L>(r, t);
+          if constexpr (KEEP_P) pv[r] = v[r];
+          lpp += v[r].x * v[r].x + v[r].y * v[r].y;
+          prow_a[n] = v[r].x;
+          prow_b[n] = v[r].y;
+        }
+      } else if (step & 1) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = times_ik(v[r], kwave<L>(idx_a<L>(r, t)));
+      } else if (step == 2) {
+        ok = mbar_wait(&kbar, pk.done & 1);
+        if (__syncthreads_or(!ok)) { bad = true; break; }
+        ++pk.done;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const int n = idx_b<L>(r, t);
+          const T ka = *row_elem<T, L>(k_buf, ra, n), kb = *row_elem<T, L>(k_buf, rb, n);
+          lk += ka * v[r].x * v[r].x + kb * v[r].y * v[r].y;
+          v[r].x *= ka;
+          v[r].y *= kb;
+        }
+        __syncthreads();   // every kappa value is in registers
+        if (threadIdx.x == 0) {
+          const long long kt = next_act(tile + stride);
+          if (kt < ntiles) issue(k_buf, &a.map_k, &kbar, pk, kt);
+        }
       }
     }
     if (bad) break;
@@ -1094,7 +1113,7 @@ __global__ void __launch_bounds__(TmaRowShape<T, L>::THREADS) k_dht_row_tma(cons
       issue(tile + stride, b ^ 1);
     }
     fft_ab<T, L, -1, kTwGlobal>(v, sm, t, twA);
-    hartley_combine<T, L, kTwGlobal>(v, t);
+    hartley_combine<T, L, true>(v, t);
     // Hartley values go to the p tile (update) or back into the r tile (setup)
     unsigned char* ob = (MODE == kDhtUpdate) ? fld(b, 2) : fld(b, 0);
     if (MODE != kDhtUpdate) __syncwarp();

@@ -84,7 +84,7 @@ def compute(name):
     prob = problem(case)
     M = orc.model_from_problem(prob, rtol=case["rtol"], maxit=5000, kind="numpy")
     t0 = time.perf_counter()
-    c_true, _ = M.forward(prob.p_true, prob.k_f_true, prob.rho_f_true)
+    c_true = M.forward(prob.p_true, prob.k_f_true, prob.rho_f_true)[0]   # its trajectory is not kept
     d = synth.labels(c_true, synth.ellipsoid_mask(prob.n), prob.seed + 7)
     del c_true
     M.iters = []

@@ -482,6 +482,34 @@ def test_gauss_newton_reduces_misfit_on_gpu():
     assert Js[-1] < 0.5 * J0
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_gauss_newton_recovers_growth_parameters_from_noise_free_data(prec):
+    """Sec. 3.1/3.2 on data the model can fit exactly: the oracle's c_true(1)
+    at 64^3, unthresholded.  With the initial condition at the truth the
+    Gauss-Newton loop recovers (k_f, rho_f) from (0.02, 6) to the truth
+    (0.05, 10); on all parameters at once it lowers the misfit by orders of
+    magnitude (the initial condition itself is not identifiable from c(1):
+    many weight vectors of the overlapping Gaussians give nearly the same
+    state, the ill-posedness the paper notes)."""
+    from paper_1907_07774_gb300 import gn
+
+    prob = synth.calibration_problem(n=64, nt=8, m=4, sigma=TWO_PI / 32)
+    M = oracle_for(prob)
+    c_true, _ = M.forward(prob.p_true, prob.k_f_true, prob.rho_f_true)
+    ctx = gpu_for(prob, prec)
+    ctx.rd_set_data(c_true)
+    npar = len(prob.p)
+    th0 = np.concatenate([prob.p_true, [prob.k_f, prob.rho_f]])
+    res = gn.gauss_newton(ctx, th0, iters=8, cg_maxit=10, forcing=1e-3, fixed=tuple(range(npar)))
+    assert np.array_equal(res.theta[:npar], prob.p_true)
+    assert abs(res.theta[-2] - prob.k_f_true) <= 1e-3 * prob.k_f_true
+    assert abs(res.theta[-1] - prob.rho_f_true) <= 1e-3 * prob.rho_f_true
+    th0 = np.concatenate([prob.p, [prob.k_f, prob.rho_f]])
+    J0 = ctx.rd_forward(prob.p, prob.k_f, prob.rho_f)
+    res = gn.gauss_newton(ctx, th0, iters=6, cg_maxit=20, forcing=1e-3)
+    assert res.misfit < 1e-2 * J0
+
+
 def test_batch_gradient_of_uneven_problems_matches_single_gradients():
     """One graph launch for several contexts of different grid sizes equals
     the per-context rd_gradient results, on two calls in a row."""
