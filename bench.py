@@ -110,6 +110,30 @@ def ncu_traffic(cls, n):
     return float(ent["bytes_per_launch"]) * (n ** 3) / float(ent.get("cells", n ** 3))
 
 
+def ncu_dram_weighted(prof, n, peak):
+    """Time-weighted DRAM throughput of the FFT/operator kernels from ncu's
+    DRAM counters: the committed per-launch DRAM bytes of each class (one
+    ncu capture on the current sources, profiles/ncu_traffic.json) times the
+    launches of this step, over the classes' live CUDA-event time.  ncu
+    replays each launch with cold caches, so its bytes bound the live ones
+    from above; None when the capture predates the sources."""
+    tot_b, tot_ms, used = 0.0, 0.0, []
+    for cls, (ms, cnt) in prof.items():
+        if not cnt:
+            continue
+        b = ncu_traffic(cls, n)
+        if b is None:
+            continue
+        tot_b += b * cnt
+        tot_ms += ms
+        used.append(cls)
+    if not used or tot_ms <= 0:
+        return None
+    gbs = tot_b / (tot_ms / 1e3) / 1e9
+    return {"gbs": gbs, "frac": gbs / peak, "classes": used,
+            "source": "profiles/ncu_traffic.json (dram__bytes_read.sum + dram__bytes_write.sum per launch)"}
+
+
 class Clocks:
     """nvidia-smi sampling during the timed region."""
 
@@ -460,6 +484,7 @@ def run_ours(args, rank, world, local):
                 "share_of_step": dms / (ms / args.steps),
                 "fft_operator_kernels_time_weighted_gbs": tot_bytes / (tot_ms / 1e3) / 1e9,
                 "fft_operator_kernels_frac": tot_bytes / (tot_ms / 1e3) / 1e9 / peak,
+                "ncu_dram": ncu_dram_weighted(prof, n, peak),
                 "timing": "per-launch CUDA events in one profiled step after the timed region (host-driven "
                           "PCG loop: its class times sum to a little more than the graph-run step)",
                 "active_tile_fraction": act_frac,

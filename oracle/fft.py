@@ -66,11 +66,20 @@ def dft_dense(x, axis, inverse=False):
     return _along(_dense_axis0, x, axis, inverse)
 
 
+# threads of the ``"scipy"`` kind (the library transform split over cores,
+# for long oracle runs on large grids)
+SCIPY_WORKERS = 1
+
+
 def fftn(x, inverse=False, kind="recursive"):
     """3D transform: one 1D transform per axis (``kind``: ``"recursive"``,
-    ``"dense"``, or ``"numpy"`` for the library routine)."""
+    ``"dense"``, ``"numpy"`` for the library routine, or ``"scipy"`` for the
+    library routine on ``SCIPY_WORKERS`` threads)."""
     if kind == "numpy":
         return np.fft.ifftn(x) if inverse else np.fft.fftn(x)
+    if kind == "scipy":
+        import scipy.fft as sf
+        return sf.ifftn(x, workers=SCIPY_WORKERS) if inverse else sf.fftn(x, workers=SCIPY_WORKERS)
     f = fft if kind == "recursive" else dft_dense
     y = np.asarray(x, dtype=np.complex128)
     for a in range(y.ndim):

@@ -27,9 +27,41 @@ __device__ __forceinline__ int wrap(int i, int n) {
   return i < 0 ? i + n : i;
 }
 
-// K fields interpolated at the point (X0, X1, X2) in index units, periodic.
-template <typename T, int K>
-__device__ __forceinline__ void interp(const T* const* u, const Geom& g, T X0, T X1, T X2, T* out) {
+// Four fields of one grid point side by side (array of structures), so that
+// the 64-point stencil of an interpolation loads each neighbour once with a
+// vector load instead of once per field.
+template <typename T>
+struct alignas(4 * sizeof(T)) V4 {
+  T x, y, z, w;
+};
+
+template <typename T>
+__device__ __forceinline__ V4<T> ldv4(const V4<T>* p) {
+  if constexpr (sizeof(T) == 4) {
+    const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+    return {v.x, v.y, v.z, v.w};
+  } else {
+    const double2 a = __ldg(reinterpret_cast<const double2*>(p));
+    const double2 b = __ldg(reinterpret_cast<const double2*>(p) + 1);
+    return {a.x, a.y, b.x, b.y};
+  }
+}
+
+// out[i] = (a[i], b[i], c[i], d ? d[i] : 0)
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_pack4(const T* __restrict__ a, const T* __restrict__ b,
+                                                    const T* __restrict__ c, const T* __restrict__ d,
+                                                    V4<T>* __restrict__ out, long long nn) {
+  for (long long i = (long long)blockIdx.x * kThreads + threadIdx.x; i < nn; i += (long long)gridDim.x * kThreads)
+    out[i] = {a[i], b[i], c[i], d ? d[i] : T(0)};
+}
+
+// Periodic tricubic Lagrange interpolation (nodes -1..2 per axis, weights
+// lag4) at the point (X0, X1, X2) in index units, for NP packed arrays of
+// four fields each: out[4 p + j] is component j of array p there.  The
+// weights are applied axis by axis (rows along axis 2 first).
+template <typename T, int NP>
+__device__ __forceinline__ void interp4(const V4<T>* const* u, const Geom& g, T X0, T X1, T X2, T* out) {
   const T f0 = floor(X0), f1 = floor(X1), f2 = floor(X2);
   T w0[4], w1[4], w2[4];
   lag4(X0 - f0, w0);
@@ -40,7 +72,7 @@ __device__ __forceinline__ void interp(const T* const* u, const Geom& g, T X0, T
 #pragma unroll
   for (int o = 0; o < 4; ++o) i2[o] = wrap(b2 + o, g.n[2]);
 #pragma unroll
-  for (int k = 0; k < K; ++k) out[k] = T(0);
+  for (int k = 0; k < 4 * NP; ++k) out[k] = T(0);
 #pragma unroll
   for (int o0 = 0; o0 < 4; ++o0) {
     const int i0 = wrap(b0 + o0, g.n[0]);
@@ -49,12 +81,21 @@ __device__ __forceinline__ void interp(const T* const* u, const Geom& g, T X0, T
       const long long row = ((long long)i0 * g.n[1] + wrap(b1 + o1, g.n[1])) * g.n[2];
       const T w01 = w0[o0] * w1[o1];
 #pragma unroll
-      for (int k = 0; k < K; ++k) {
-        const T* p = u[k] + row;
-        // read-only path: the gathered fields are never written by this kernel
-        const T acc = w2[0] * __ldg(p + i2[0]) + w2[1] * __ldg(p + i2[1]) + w2[2] * __ldg(p + i2[2]) +
-                      w2[3] * __ldg(p + i2[3]);
-        out[k] += w01 * acc;
+      for (int q = 0; q < NP; ++q) {
+        const V4<T>* p = u[q] + row;
+        V4<T> acc = {T(0), T(0), T(0), T(0)};
+#pragma unroll
+        for (int o2 = 0; o2 < 4; ++o2) {
+          const V4<T> e = ldv4(p + i2[o2]);
+          acc.x += w2[o2] * e.x;
+          acc.y += w2[o2] * e.y;
+          acc.z += w2[o2] * e.z;
+          acc.w += w2[o2] * e.w;
+        }
+        out[4 * q + 0] += w01 * acc.x;
+        out[4 * q + 1] += w01 * acc.y;
+        out[4 * q + 2] += w01 * acc.z;
+        out[4 * q + 3] += w01 * acc.w;
       }
     }
   }
@@ -72,6 +113,7 @@ __device__ __forceinline__ void coords(const Geom& g, long long i, int& i0, int&
 template <typename T>
 struct FeetArgs {
   const T* v[3];
+  const V4<T>* vp;   // (v0, v1, v2, 0) packed for the interpolation
   T* d[3];
   Geom g;
   T cdt[3];   // sign * dt / h_a
@@ -83,8 +125,8 @@ __global__ void __launch_bounds__(kThreads) k_feet(FeetArgs<T> a) {
     int i0, i1, i2;
     coords(a.g, i, i0, i1, i2);
     const T v0 = a.v[0][i], v1 = a.v[1][i], v2 = a.v[2][i];
-    T vy[3];
-    interp<T, 3>(a.v, a.g, T(i0) + a.cdt[0] * v0, T(i1) + a.cdt[1] * v1, T(i2) + a.cdt[2] * v2, vy);
+    T vy[4];
+    interp4<T, 1>(&a.vp, a.g, T(i0) + a.cdt[0] * v0, T(i1) + a.cdt[1] * v1, T(i2) + a.cdt[2] * v2, vy);
     a.d[0][i] = T(0.5) * a.cdt[0] * (v0 + vy[0]);
     a.d[1][i] = T(0.5) * a.cdt[1] * (v1 + vy[1]);
     a.d[2][i] = T(0.5) * a.cdt[2] * (v2 + vy[2]);
@@ -104,6 +146,7 @@ struct InterpArgs {
   const T* s[3];    // kIpInc: source at the previous level
   const T* s1[3];   // kIpInc: source at the new level
   const T* D;       // kIpAdj: div v
+  const V4<T>* pk[2];   // the gathered fields packed: (u0, u1, u2, D or 0), (s0, s1, s2, 0)
   T* out[3];
   Geom g;
   T dt;
@@ -111,20 +154,21 @@ struct InterpArgs {
 
 template <typename T, int MODE>
 __global__ void __launch_bounds__(kThreads) k_interp(InterpArgs<T> a) {
-  constexpr int K = (MODE == kIpPlain) ? 3 : (MODE == kIpAdj ? 4 : 6);
-  const T* src[K];
-#pragma unroll
-  for (int k = 0; k < 3; ++k) src[k] = a.u[k];
-  if constexpr (MODE == kIpAdj) src[3] = a.D;
-  if constexpr (MODE == kIpInc) {
-#pragma unroll
-    for (int k = 0; k < 3; ++k) src[3 + k] = a.s[k];
-  }
+  // gathered fields, packed by k_pack4: plain (u, 0), adjoint (l, D),
+  // incremental (u, 0) and (s, 0); r[4 q + j] is field j of array q
+  constexpr int NP = (MODE == kIpInc) ? 2 : 1;
   for (long long i = (long long)blockIdx.x * kThreads + threadIdx.x; i < a.g.nn; i += (long long)gridDim.x * kThreads) {
     int i0, i1, i2;
     coords(a.g, i, i0, i1, i2);
-    T r[K];
-    interp<T, K>(src, a.g, T(i0) + a.d[0][i], T(i1) + a.d[1][i], T(i2) + a.d[2][i], r);
+    T r4[4 * NP];
+    interp4<T, NP>(a.pk, a.g, T(i0) + a.d[0][i], T(i1) + a.d[1][i], T(i2) + a.d[2][i], r4);
+    T r[6];
+    r[0] = r4[0];
+    r[1] = r4[1];
+    r[2] = r4[2];
+    r[3] = (MODE == kIpInc) ? r4[4 * (NP - 1)] : r4[3];
+    r[4] = r4[4 * (NP - 1) + 1];
+    r[5] = r4[4 * (NP - 1) + 2];
     if constexpr (MODE == kIpPlain) {
 #pragma unroll
       for (int k = 0; k < 3; ++k) a.out[k][i] = r[k];

@@ -78,11 +78,11 @@ def direction(np_total):
     return synth.random_directions(1, np_total, DIR_SEED)[0]
 
 
-def compute(name):
+def compute(name, fft_kind="numpy"):
     case = CASES[name]
     n = case["n"]
     prob = problem(case)
-    M = orc.model_from_problem(prob, rtol=case["rtol"], maxit=5000, kind="numpy")
+    M = orc.model_from_problem(prob, rtol=case["rtol"], maxit=5000, kind=fft_kind)
     t0 = time.perf_counter()
     c_true = M.forward(prob.p_true, prob.k_f_true, prob.rho_f_true)[0]   # its trajectory is not kept
     d = synth.labels(c_true, synth.ellipsoid_mask(prob.n), prob.seed + 7)
@@ -134,8 +134,15 @@ def load(name):
 
 
 if __name__ == "__main__":
+    # optional second argument: threads for the library FFT (scipy), which
+    # only shortens the run; the numpy and scipy transforms agree to rounding
     name = sys.argv[1]
-    out, arrays = compute(name)
+    threads = int(sys.argv[2]) if len(sys.argv) > 2 else 0
+    if threads > 0:
+        from oracle import fft as _fft
+        _fft.SCIPY_WORKERS = threads
+    out, arrays = compute(name, "scipy" if threads > 0 else "numpy")
+    out["case"]["fft"] = f"scipy, {threads} threads" if threads > 0 else "numpy"
     js, nz = paths(name)
     np.savez_compressed(nz, **arrays)
     with open(js, "w") as f:

@@ -415,3 +415,20 @@ def test_coupling_field_euler_identity(small_problem):
     rhs = k_f * g[-2] + rho_f * g[-1]
     assert abs(lhs - rhs) <= 1e-12 * abs(rhs)
     assert np.all(q[2] == 0.0)
+
+
+def test_threaded_library_fft_matches_the_recursive_fft():
+    """The "scipy" kind (library transform on several threads, used to shorten
+    long oracle runs) agrees with the oracle's own recursive FFT."""
+    from oracle import fft as F
+    rng = np.random.default_rng(9)
+    x = rng.standard_normal((8, 12, 6)) + 1j * rng.standard_normal((8, 12, 6))
+    old = F.SCIPY_WORKERS
+    try:
+        F.SCIPY_WORKERS = 2
+        for inv in (False, True):
+            want = F.fftn(x, inverse=inv, kind="recursive")
+            got = F.fftn(x, inverse=inv, kind="scipy")
+            assert np.abs(got - want).max() <= 1e-13 * np.abs(want).max()
+    finally:
+        F.SCIPY_WORKERS = old
