@@ -85,9 +85,14 @@ def measured_peaks():
 
 
 def csrc_hash():
+    """Hash of the CUDA sources of the tumor solver (the registration and the
+    allocation-free entry point are other translation units and do not
+    change the tumor kernels)."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_1907_07774_gb300", "csrc")
     for f in sorted(os.listdir(d)):
+        if f.startswith("rd_reg") or f == "rd_noalloc.cu":
+            continue
         h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -435,6 +440,7 @@ def run_ours(args, rank, world, local):
     for _ in range(args.warmup):
         J, g = ctx.rd_gradient(p, k_f, rho_f)
     iters, solves = ctx.rd_last_pcg_iters(), ctx.rd_last_pcg_solves()
+    graph_solves = ctx.rd_last_graph_solves()
 
     def barrier():
         if dist is not None:
@@ -594,6 +600,7 @@ def run_ours(args, rank, world, local):
                                                                  "working set > 2 GiB)",
                            "parallelism": "replicas" if world > 1 else "single"},
                 "misfit": J, "pcg_iters_per_step": iters, "pcg_solves_per_step": solves,
+                "pcg_graph_solves_per_step": graph_solves,
                 "data_labels": data_src, "vs_fp64_oracle": vs_oracle,
                 "gpu_launches": launches_per_step * args.steps, "clocks": clocks, "roofline": roofline, "e2e": e2e,
                 "cpu_baseline": cpu, "fp64": fp64, "checkpointed": ckpt, "batch": batch,

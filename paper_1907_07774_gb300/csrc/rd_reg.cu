@@ -46,7 +46,7 @@ struct RegEngine final : RegBase {
   T *mA[3], *mP[3], *c = nullptr, *q[3];
   T *v[3], *vt[3], *d[3], *dp[3], *D = nullptr, *phi = nullptr, *w1 = nullptr, *w2 = nullptr;
   T *lam[3], *lam2[3], *mt[3], *mt2[3], *s0[3], *s1[3], *b[3], *t3[3], *gf[3];
-  V4<T>* pk[2] = {nullptr, nullptr};   // packed fields for the interpolation gathers
+  V4<T>* pk[1] = {nullptr};   // packed fields for the interpolation gathers
   std::vector<T*> lev;   // (nt + 1) x 3 transported anatomy fields
   double* stage[3];
   double* part = nullptr;
@@ -99,7 +99,7 @@ struct RegEngine final : RegBase {
     for (T** f : fields3)
       for (int k = 0; k < 3; ++k) ok = ok && alloc(&f[k], fb);
     ok = ok && alloc(&c, fb) && alloc(&D, fb) && alloc(&phi, fb) && alloc(&w1, fb) && alloc(&w2, fb);
-    for (int k = 0; k < 2; ++k) ok = ok && alloc(&pk[k], sizeof(V4<T>) * nn);
+    ok = ok && alloc(&pk[0], sizeof(V4<T>) * nn);
     lev.assign(size_t(cfg.nt + 1) * 3, nullptr);
     for (auto& p : lev) ok = ok && alloc(&p, fb);
     for (int k = 0; k < 3; ++k) ok = ok && alloc(&stage[k], sizeof(double) * nn);
@@ -306,11 +306,11 @@ struct RegEngine final : RegBase {
   template <int MODE>
   cudaError_t interp_step(const InterpArgs<T>& a0) {
     InterpArgs<T> a = a0;
-    cudaError_t e = pack4(a.u[0], a.u[1], a.u[2], MODE == kIpAdj ? a.D : nullptr, pk[0]);
-    if (e == cudaSuccess && MODE == kIpInc) e = pack4(a.s[0], a.s[1], a.s[2], nullptr, pk[1]);
-    if (e != cudaSuccess) return e;
-    a.pk[0] = pk[0];
-    a.pk[1] = pk[1];
+    if (MODE != kIpInc) {
+      const cudaError_t e = pack4(a.u[0], a.u[1], a.u[2], MODE == kIpAdj ? a.D : nullptr, pk[0]);
+      if (e != cudaSuccess) return e;
+      a.pk[0] = pk[0];
+    }
     k_interp<T, MODE><<<eblocks(reinterpret_cast<const void*>(k_interp<T, MODE>)), kThreads, 0, stream>>>(a);
     return cudaGetLastError();
   }

@@ -27,6 +27,41 @@ __device__ __forceinline__ int wrap(int i, int n) {
   return i < 0 ? i + n : i;
 }
 
+// K separate fields interpolated at the point (X0, X1, X2) in index units,
+// periodic: the same tricubic Lagrange stencil as interp4, one scalar load
+// per field and neighbour (used where packing would waste loaded bytes).
+template <typename T, int K>
+__device__ __forceinline__ void interp_fields(const T* const* u, const Geom& g, T X0, T X1, T X2, T* out) {
+  const T f0 = floor(X0), f1 = floor(X1), f2 = floor(X2);
+  T w0[4], w1[4], w2[4];
+  lag4(X0 - f0, w0);
+  lag4(X1 - f1, w1);
+  lag4(X2 - f2, w2);
+  const int b0 = int(f0) - 1, b1 = int(f1) - 1, b2 = int(f2) - 1;
+  int i2[4];
+#pragma unroll
+  for (int o = 0; o < 4; ++o) i2[o] = wrap(b2 + o, g.n[2]);
+#pragma unroll
+  for (int k = 0; k < K; ++k) out[k] = T(0);
+#pragma unroll
+  for (int o0 = 0; o0 < 4; ++o0) {
+    const int i0 = wrap(b0 + o0, g.n[0]);
+#pragma unroll
+    for (int o1 = 0; o1 < 4; ++o1) {
+      const long long row = ((long long)i0 * g.n[1] + wrap(b1 + o1, g.n[1])) * g.n[2];
+      const T w01 = w0[o0] * w1[o1];
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const T* p = u[k] + row;
+        // read-only path: the gathered fields are never written by this kernel
+        const T acc = w2[0] * __ldg(p + i2[0]) + w2[1] * __ldg(p + i2[1]) + w2[2] * __ldg(p + i2[2]) +
+                      w2[3] * __ldg(p + i2[3]);
+        out[k] += w01 * acc;
+      }
+    }
+  }
+}
+
 // Four fields of one grid point side by side (array of structures), so that
 // the 64-point stencil of an interpolation loads each neighbour once with a
 // vector load instead of once per field.
@@ -146,7 +181,7 @@ struct InterpArgs {
   const T* s[3];    // kIpInc: source at the previous level
   const T* s1[3];   // kIpInc: source at the new level
   const T* D;       // kIpAdj: div v
-  const V4<T>* pk[2];   // the gathered fields packed: (u0, u1, u2, D or 0), (s0, s1, s2, 0)
+  const V4<T>* pk[1];   // plain/adjoint: the gathered fields packed, (u0, u1, u2, D or 0)
   T* out[3];
   Geom g;
   T dt;
@@ -154,21 +189,20 @@ struct InterpArgs {
 
 template <typename T, int MODE>
 __global__ void __launch_bounds__(kThreads) k_interp(InterpArgs<T> a) {
-  // gathered fields, packed by k_pack4: plain (u, 0), adjoint (l, D),
-  // incremental (u, 0) and (s, 0); r[4 q + j] is field j of array q
-  constexpr int NP = (MODE == kIpInc) ? 2 : 1;
+  // plain and adjoint: the gathered fields packed by k_pack4, (u, 0) and
+  // (l, D), one vector load per neighbour; incremental: six separate fields
+  // (u and s), where packing would load two pad values per neighbour
+  const T* src6[6] = {a.u[0], a.u[1], a.u[2], a.s[0], a.s[1], a.s[2]};
   for (long long i = (long long)blockIdx.x * kThreads + threadIdx.x; i < a.g.nn; i += (long long)gridDim.x * kThreads) {
     int i0, i1, i2;
     coords(a.g, i, i0, i1, i2);
-    T r4[4 * NP];
-    interp4<T, NP>(a.pk, a.g, T(i0) + a.d[0][i], T(i1) + a.d[1][i], T(i2) + a.d[2][i], r4);
+    const T X0 = T(i0) + a.d[0][i], X1 = T(i1) + a.d[1][i], X2 = T(i2) + a.d[2][i];
     T r[6];
-    r[0] = r4[0];
-    r[1] = r4[1];
-    r[2] = r4[2];
-    r[3] = (MODE == kIpInc) ? r4[4 * (NP - 1)] : r4[3];
-    r[4] = r4[4 * (NP - 1) + 1];
-    r[5] = r4[4 * (NP - 1) + 2];
+    if constexpr (MODE == kIpInc) {
+      interp_fields<T, 6>(src6, a.g, X0, X1, X2, r);
+    } else {
+      interp4<T, 1>(a.pk, a.g, X0, X1, X2, r);
+    }
     if constexpr (MODE == kIpPlain) {
 #pragma unroll
       for (int k = 0; k < 3; ++k) a.out[k][i] = r[k];
