@@ -199,16 +199,20 @@ class Clocks:
 
 
 # algorithmic fields moved per launch of each kernel class, over the whole grid
+# (the CG update reads r and q and writes r and H_2 r; x += alpha p rides on
+# the next iteration's direction kernel)
 FIELDS_PER_LAUNCH = {"op_axis01": 4, "op_axis2": 3, "pcg_opx": 5, "dht_plain": 2, "dht_sym": 2,
-                     "dht_setup": 2, "dht_update": 7, "grad": 4}
+                     "dht_setup": 2, "dht_update": 4, "grad": 4}
 
 
-def fields_per_launch(active):
+def fields_per_launch(active, iters=0, solves=0):
     """Fields each class must move per launch once the tiles where kappa
     vanishes are skipped (rd_active_tiles): the strided operator passes move
     u, kappa, q in and q out only on active tiles (axes 0 and 1 alternate);
     the direction kernel reads kappa only on active row tiles; the k_f
-    gradient passes (axes 2, 1, 0) skip inactive strided tiles."""
+    gradient passes (axes 2, 1, 0) skip inactive strided tiles.  From the
+    second iteration of a solve on, the direction kernel also reads and
+    writes x (the deferred x += alpha p)."""
     f0 = active["axis0"][0] / max(1, active["axis0"][1])
     f1 = active["axis1"][0] / max(1, active["axis1"][1])
     fr = active["rows"][0] / max(1, active["rows"][1])
@@ -216,6 +220,8 @@ def fields_per_launch(active):
     out["op_axis01"] = 4 * 0.5 * (f0 + f1)
     out["pcg_opx"] = 4 + fr
     out["grad"] = 4 * (1 + f0 + f1) / 3
+    if iters > 0:
+        out["pcg_opx"] += 2 * max(0, iters - solves) / iters
     return out, {"axis0": f0, "axis1": f1, "rows": fr}
 
 
@@ -473,7 +479,7 @@ def run_ours(args, rank, world, local):
 
     # ---- roofline of the dominant kernel class
     esz = 4
-    fpl, act_frac = fields_per_launch(ctx.rd_active_tiles())
+    fpl, act_frac = fields_per_launch(ctx.rd_active_tiles(), iters, solves)
     dom = max((k for k in prof if k in fpl), key=lambda k: prof[k][0])
     dms, dcount = prof[dom]
     alg_bytes = fpl[dom] * n ** 3 * esz

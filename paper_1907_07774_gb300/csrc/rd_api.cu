@@ -584,6 +584,7 @@ struct Engine : EngineBase {
       a.w = W2;
       a.p = P;
       a.q = Q;
+      a.x = X;   // the previous iteration's x += alpha p rides on this kernel
       a.kappa = f[F_KAPPA1];
       a.g = g;
       a.twA = twA[lidx(g.n[2])];
@@ -616,8 +617,6 @@ struct Engine : EngineBase {
     }
     {
       DhtArgs<T> a = dht_args(2, nullptr, W1);
-      a.x = X;
-      a.p = P;
       a.r = R;
       a.q = Q;
       a.fin = fin(kFinRr);
@@ -730,9 +729,13 @@ struct Engine : EngineBase {
     stream = outer;
     if (e != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess)
       return cuda_fail(e != cudaSuccess ? e : (e2 != cudaSuccess ? e2 : e3), "while body");
+    if ((e = enqueue_final()) != cudaSuccess) return cuda_fail(e, "pcg final update");
     ++last_graph_solves;
     return RD_OK;
   }
+
+  // The last deferred x += alpha p of a solve (see DhtArgs).
+  cudaError_t enqueue_final() { return L_::cg_final(f[F_X], f[F_P], st, nn, stream); }
 
   // Preconditioned CG on (I - s k_f A1) x = f with x0 = 0; f in F_R on entry;
   // the solution is left in F_X and the final residual in F_R.  After two
@@ -756,6 +759,7 @@ struct Engine : EngineBase {
       }
       if (pcg_exec) {
         if ((e = cudaGraphLaunch(pcg_exec, stream)) != cudaSuccess) return cuda_fail(e, "pcg graph launch");
+        if ((e = enqueue_final()) != cudaSuccess) return cuda_fail(e, "pcg final update");
         ++last_graph_solves;
         return RD_OK;
       }
@@ -771,6 +775,7 @@ struct Engine : EngineBase {
       if (hst->done) break;
       if ((e = enqueue_iteration(0)) != cudaSuccess) return cuda_fail(e, "pcg iteration");
     }
+    if ((e = enqueue_final()) != cudaSuccess) return cuda_fail(e, "pcg final update");
     return RD_OK;
   }
 

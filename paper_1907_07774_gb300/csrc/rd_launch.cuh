@@ -52,6 +52,7 @@ struct Launch {
   static cudaError_t combine(const T* qk, const T* qr, double ca, double cb, double* out, long long nn,
                              cudaStream_t s);
   static cudaError_t normsq(const NormArgs<T>& a, cudaStream_t s);
+  static cudaError_t cg_final(T* x, const T* p, const PcgState* st, long long nn, cudaStream_t s);
 };
 
 extern template struct Launch<float>;

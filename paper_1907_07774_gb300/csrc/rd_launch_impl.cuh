@@ -196,8 +196,7 @@ cudaError_t Launch<T>::dht(int L, int mode, const DhtArgs<T>& a, cudaStream_t s)
   if (a.axis == 2 && (mode == kDhtSetup || mode == kDhtUpdate) &&
       !tuned_pencil(mode == kDhtSetup ? kcDhtSetup : kcDhtUpdate, L)) {
     const void* rr = (mode == kDhtSetup) ? (const void*)a.in : (const void*)a.r;
-    const bool al = aligned16(rr) && aligned16(a.out) &&
-                    (mode == kDhtSetup || (aligned16(a.x) && aligned16(a.p) && aligned16(a.q)));
+    const bool al = aligned16(rr) && aligned16(a.out) && (mode == kDhtSetup || aligned16(a.q));
     if (al) {
       RD_DISPATCH_L(L, {
         using TS = TmaRowShape<T, LL>;
@@ -207,13 +206,9 @@ cudaError_t Launch<T>::dht(int L, int mode, const DhtArgs<T>& a, cudaStream_t s)
           bool ok = rows % TS::ROWS == 0 && row_map(&t.map_r, rr, a.g, sizeof(T), TS::ROWS) &&
                     row_map(&t.map_out, a.out, a.g, sizeof(T), TS::ROWS);
           if (ok && mode == kDhtUpdate)
-            ok = row_map(&t.map_x, a.x, a.g, sizeof(T), TS::ROWS) && row_map(&t.map_p, a.p, a.g, sizeof(T), TS::ROWS) &&
-                 row_map(&t.map_q, a.q, a.g, sizeof(T), TS::ROWS);
-          else if (ok) {
-            t.map_x = t.map_r;
-            t.map_p = t.map_r;
+            ok = row_map(&t.map_q, a.q, a.g, sizeof(T), TS::ROWS);
+          else if (ok)
             t.map_q = t.map_r;
-          }
           if (ok) {
             t.g = a.g;
             t.twA = a.twA;
@@ -282,16 +277,19 @@ template <typename T>
 cudaError_t Launch<T>::pcg_opx(int L, const PcgOpxArgs<T>& a, cudaStream_t s) {
   using namespace detail;
   const long long npairs = a.g.nn / L / 2;
-  if (!tuned_pencil(kcPcgOpx, L) && aligned16(a.w) && aligned16(a.p) && aligned16(a.q) && aligned16(a.kappa)) {
+  if (!tuned_pencil(kcPcgOpx, L) && aligned16(a.w) && aligned16(a.p) && aligned16(a.q) && aligned16(a.kappa) &&
+      (!a.x || aligned16(a.x))) {
     RD_DISPATCH_L(L, {
       using TS = TmaRowShape<T, LL>;
       if constexpr (TS::OK) {
         const long long rows = a.g.nn / LL;
         PcgOpxTmaArgs<T> t;
         if (rows % TS::ROWS == 0 && row_map(&t.map_w, a.w, a.g, sizeof(T), TS::ROWS) &&
-            row_map(&t.map_k, a.kappa, a.g, sizeof(T), TS::ROWS) && row_map(&t.map_p, a.p, a.g, sizeof(T), TS::ROWS)) {
+            row_map(&t.map_k, a.kappa, a.g, sizeof(T), TS::ROWS) && row_map(&t.map_p, a.p, a.g, sizeof(T), TS::ROWS) &&
+            (!a.x || row_map(&t.map_x, a.x, a.g, sizeof(T), TS::ROWS))) {
           t.p = a.p;
           t.q = a.q;
+          t.x = a.x;
           t.g = a.g;
           t.twA = a.twA;
           t.twB = a.twB;
@@ -415,6 +413,14 @@ cudaError_t Launch<T>::to_f64(const T* in, double* out, long long nn, double sca
 template <typename T>
 cudaError_t Launch<T>::normsq(const NormArgs<T>& a, cudaStream_t s) {
   return detail::launch_pencil(k_normsq<T>, 0, (a.nn + kThreads - 1) / kThreads, a, s, kcPointwise);
+}
+
+template <typename T>
+cudaError_t Launch<T>::cg_final(T* x, const T* p, const PcgState* st, long long nn, cudaStream_t s) {
+  const void* fn = reinterpret_cast<const void*>(k_cg_final<T>);
+  int grid = detail::grid_for(fn, 0, (nn + kThreads - 1) / kThreads);
+  k_cg_final<T><<<grid, kThreads, 0, s>>>(x, p, st, nn);
+  return cudaGetLastError();
 }
 
 template <typename T>

@@ -229,7 +229,7 @@ __global__ void __launch_bounds__(kThreads) k_op(OpArgs<T> a) {
 enum DhtMode {
   kDhtPlain = 0,   // out = H_axis(in)                              (axis 1)
   kDhtSetup = 1,   // ff = ||in||^2 ; out = H_2(in)                 (axis 2)
-  kDhtUpdate = 2,  // x += alpha p; r -= alpha q; rr; out = H_2(r)  (axis 2)
+  kDhtUpdate = 2,  // r -= alpha q; rr; out = H_2(r)                (axis 2)
   kDhtSym = 3      // out = H_0 S' H_0 in = F_0^-1 S' F_0 in; rz = sum S' (H_0 in)^2   (axis 0)
 };
 
@@ -237,9 +237,9 @@ template <typename T>
 struct DhtArgs {
   const T* in;
   T* out;
-  T* x;          // update mode
+  T* x;          // unused by the passes (kept for callers' convenience)
   const T* p;
-  T* r;
+  T* r;          // update mode
   const T* q;
   int axis;
   Geom g;
@@ -279,14 +279,10 @@ __global__ void __launch_bounds__(kThreads) k_dht(DhtArgs<T> a) {
         cpx<T> rv = {T(0), T(0)};
         if (act) {
           const long long off = (long long)idx_a<L>(r, t) * st;
-          cpx<T> xv = ld2<T, CONTIG>(a.x, b0, b1, off), pv = ld2<T, CONTIG>(a.p, b0, b1, off);
-          cpx<T> qv = ld2<T, CONTIG>(a.q, b0, b1, off);
+          const cpx<T> qv = ld2<T, CONTIG>(a.q, b0, b1, off);
           rv = ld2<T, CONTIG>(a.r, b0, b1, off);
-          xv.x += alpha * pv.x;
-          xv.y += alpha * pv.y;
           rv.x -= alpha * qv.x;
           rv.y -= alpha * qv.y;
-          st2<T, CONTIG>(a.x, b0, b1, off, xv);
           st2<T, CONTIG>(a.r, b0, b1, off, rv);
           loc += rv.x * rv.x + rv.y * rv.y;
         }
@@ -332,11 +328,17 @@ __global__ void __launch_bounds__(kThreads) k_dht(DhtArgs<T> a) {
 // z = H_2(w) (last factor of M^-1 r, scale folded into S'); p = z + beta p;
 // q = p - s k_f d_2(kappa d_2 p).  Fields are written at layout-B positions
 // of each pencil, which is just a permutation inside the pencil.
+// The CG iterate's update x += alpha p is deferred by one iteration: the
+// direction kernel of the next iteration applies it while it holds the old p
+// (alpha is still the previous iteration's there), and k_cg_final applies the
+// last one after the loop; the update kernel then moves only r and q.  The
+// sum of alpha_k p_k is formed in the same order as without the deferral.
 template <typename T>
 struct PcgOpxArgs {
   const T* w;
   T* p;
   T* q;
+  T* x;          // CG iterate (deferred update; null: none)
   const T* kappa;
   Geom g;
   const cpx<T>* twA;
@@ -357,6 +359,10 @@ __global__ void __launch_bounds__(kThreads) k_pcg_opx(PcgOpxArgs<T> a) {
   const long long npairs = a.g.nn / L / 2;
   const double betad = a.st->beta;
   const T beta = T(betad);
+  // from the second iteration on (st->it counts completed iterations): the
+  // previous iteration's x += alpha p with the old p read here anyway
+  const bool xupd = a.x && a.st->it > 0;
+  const T alpha = xupd ? T(a.st->alpha) : T(0);
   const T coef = T(-a.prm->s * a.prm->k_f / (double(L) * double(L)));
   double red_pp = 0.0, red_k = 0.0;
   for (long long base = (long long)blockIdx.x * G; base < npairs; base += (long long)gridDim.x * G) {
@@ -374,10 +380,16 @@ __global__ void __launch_bounds__(kThreads) k_pcg_opx(PcgOpxArgs<T> a) {
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         const long long off = idx_b<L>(r, t);
-        if (betad != 0.0) {
-          cpx<T> po = ld2<T, true>(a.p, b0, b1, off);
+        if (betad != 0.0 || xupd) {
+          const cpx<T> po = ld2<T, true>(a.p, b0, b1, off);
           v[r].x += beta * po.x;
           v[r].y += beta * po.y;
+          if (xupd) {
+            cpx<T> xv = ld2<T, true>(a.x, b0, b1, off);
+            xv.x += alpha * po.x;
+            xv.y += alpha * po.y;
+            st2<T, true>(a.x, b0, b1, off, xv);
+          }
         }
         lpp += v[r].x * v[r].x + v[r].y * v[r].y;
         st2<T, true>(a.p, b0, b1, off, v[r]);
@@ -726,6 +738,17 @@ __global__ void __launch_bounds__(kThreads) k_normsq(NormArgs<T> a) {
   }
   double vv[1] = {red};
   reduce_finish<1>(vv, a.fin);
+}
+
+// The last deferred CG update after the iteration loop: x += alpha p when
+// at least one iteration ran.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_cg_final(T* __restrict__ x, const T* __restrict__ p,
+                                                       const PcgState* st, long long nn) {
+  if (st->it <= 0) return;
+  const T alpha = T(st->alpha);
+  for (long long i = (long long)blockIdx.x * kThreads + threadIdx.x; i < nn; i += (long long)gridDim.x * kThreads)
+    x[i] += alpha * p[i];
 }
 
 // out = ca qk + cb qr in FP64 (coupling field of one tissue class)

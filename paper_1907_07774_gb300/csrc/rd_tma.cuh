@@ -691,9 +691,9 @@ struct TmaRowShape {
   static constexpr int XBYTES = PAIRS * XSTRIDE * int(sizeof(cpx<T>));
   static constexpr bool OK = (THREADS >= 32) && (THREADS % 32 == 0);
   static constexpr int TWBYTES = 0;   // twiddles are read from global memory (kTwGlobal)
-  static constexpr size_t OPX_SMEM = 3 * size_t(TILE_BYTES) + XBYTES + TWBYTES + 128;
+  static constexpr size_t OPX_SMEM = 4 * size_t(TILE_BYTES) + XBYTES + TWBYTES + 128;
   static constexpr size_t OPROW_SMEM = 2 * size_t(TILE_BYTES) + XBYTES + TWBYTES + 128;
-  static constexpr size_t UPD_SMEM = 8 * size_t(TILE_BYTES) + XBYTES + TWBYTES + 1024;
+  static constexpr size_t UPD_SMEM = 4 * size_t(TILE_BYTES) + XBYTES + TWBYTES + 1024;
   static constexpr size_t SETUP_SMEM = 2 * size_t(TILE_BYTES) + XBYTES + TWBYTES + 1024;
 };
 
@@ -828,8 +828,10 @@ struct PcgOpxTmaArgs {
   CUtensorMap map_w;
   CUtensorMap map_k;
   CUtensorMap map_p;
+  CUtensorMap map_x;
   T* p;          // p is read through map_p and rewritten in place
   T* q;
+  T* x;          // CG iterate: the deferred x += alpha p (see PcgOpxArgs; null: none)
   Geom g;
   const cpx<T>* twA;
   const cpx<T>* twB;
@@ -859,8 +861,9 @@ __global__ void __launch_bounds__(TmaRowShape<T, L>::THREADS) k_pcg_opx_tma(cons
   unsigned char* w_buf = smem;
   unsigned char* k_buf = smem + TB;
   unsigned char* p_buf = smem + 2 * TB;
-  cpx<T>* xbuf = reinterpret_cast<cpx<T>*>(smem + 3 * TB);
-  cpx<T>* tws = reinterpret_cast<cpx<T>*>(smem + 3 * TB + S::XBYTES);
+  unsigned char* x_buf = smem + 3 * TB;
+  cpx<T>* xbuf = reinterpret_cast<cpx<T>*>(smem + 4 * TB);
+  cpx<T>* tws = reinterpret_cast<cpx<T>*>(smem + 4 * TB + S::XBYTES);
   const cpx<T>* twA = a.twA;   // read through L1 (kTwGlobal)
   const cpx<T>* twB = a.twB;
   (void)tws;
@@ -869,14 +872,25 @@ __global__ void __launch_bounds__(TmaRowShape<T, L>::THREADS) k_pcg_opx_tma(cons
   cpx<T>* sm = xbuf + g * S::XSTRIDE;
   const long long ntiles = a.g.nn / L / S::ROWS;
   const double betad = a.st->beta;
-  const bool use_p = (betad != 0.0);
+  // from the second iteration on (st->it counts completed iterations) the
+  // old p also serves the deferred x += alpha p of the previous iteration
+  const bool xupd = a.x && a.st->it > 0;
+  const bool use_p = (betad != 0.0) || xupd;
   const T beta = T(betad);
+  const T alpha = xupd ? T(a.st->alpha) : T(0);
   const T coef = T(-a.prm->s * a.prm->k_f / (double(L) * double(L)));
   TmaPending pw, pk, pp;
   auto issue = [&](unsigned char* dst, const CUtensorMap* map, uint64_t* bar, TmaPending& pd, long long tile) {
     mbar_expect_tx(bar, TB);
     tma_load2(dst, map, 0, int(tile * S::ROWS), bar);
     ++pd.issued;
+  };
+  // old p and, with the deferred update, x of the same tile on one barrier
+  auto issue_px = [&](long long tile) {
+    mbar_expect_tx(&pbar, xupd ? 2 * TB : TB);
+    tma_load2(p_buf, &a.map_p, 0, int(tile * S::ROWS), &pbar);
+    if (xupd) tma_load2(x_buf, &a.map_x, 0, int(tile * S::ROWS), &pbar);
+    ++pp.issued;
   };
   if (threadIdx.x == 0) {
     mbar_init(&wbar, 1);
@@ -895,7 +909,7 @@ __global__ void __launch_bounds__(TmaRowShape<T, L>::THREADS) k_pcg_opx_tma(cons
     issue(w_buf, &a.map_w, &wbar, pw, t0);
     const long long kt = next_act(t0);
     if (kt < ntiles) issue(k_buf, &a.map_k, &kbar, pk, kt);
-    if (use_p) issue(p_buf, &a.map_p, &pbar, pp, t0);
+    if (use_p) issue_px(t0);
   }
   bool bad = false;
   double red_pp = 0.0, red_k = 0.0;
@@ -945,14 +959,21 @@ __global__ void __launch_bounds__(TmaRowShape<T, L>::THREADS) k_pcg_opx_tma(cons
           ok = mbar_wait(&pbar, i & 1);
           if (__syncthreads_or(!ok)) { bad = true; break; }
           ++pp.done;
+          T* xrow_a = xupd ? a.x + (tile * S::ROWS + ra) * L : nullptr;
+          T* xrow_b = xupd ? a.x + (tile * S::ROWS + rb) * L : nullptr;
 #pragma unroll
           for (int r = 0; r < R; ++r) {
             const int n = idx_b<L>(r, t);
-            v[r].x += beta * *row_elem<T, L>(p_buf, ra, n);
-            v[r].y += beta * *row_elem<T, L>(p_buf, rb, n);
+            const T pa = *row_elem<T, L>(p_buf, ra, n), pb = *row_elem<T, L>(p_buf, rb, n);
+            v[r].x += beta * pa;
+            v[r].y += beta * pb;
+            if (xupd) {
+              xrow_a[n] = *row_elem<T, L>(x_buf, ra, n) + alpha * pa;
+              xrow_b[n] = *row_elem<T, L>(x_buf, rb, n) + alpha * pb;
+            }
           }
-          __syncthreads();   // every old p value is in registers
-          if (threadIdx.x == 0 && more) issue(p_buf, &a.map_p, &pbar, pp, tile + stride);
+          __syncthreads();   // every old p (and x) value is in registers
+          if (threadIdx.x == 0 && more) issue_px(tile + stride);
         }
 #pragma unroll
         for (int r = 0; r < R; ++r) {
@@ -1019,8 +1040,6 @@ __global__ void __launch_bounds__(TmaRowShape<T, L>::THREADS) k_pcg_opx_tma(cons
 
 template <typename T>
 struct DhtRowTmaArgs {
-  CUtensorMap map_x;
-  CUtensorMap map_p;
   CUtensorMap map_r;
   CUtensorMap map_q;
   CUtensorMap map_out;
@@ -1032,15 +1051,16 @@ struct DhtRowTmaArgs {
 };
 
 // Setup: ff = ||r||^2, out = H_2(r).
-// Update: x += alpha p, r -= alpha q, rr = ||r||^2, out = H_2(r).
+// Update: r -= alpha q, rr = ||r||^2, out = H_2(r) (the iterate's x += alpha p
+// is deferred to the next iteration's first Hartley pass, see DhtArgs).
 template <typename T, int L, int MODE>
 __global__ void __launch_bounds__(TmaRowShape<T, L>::THREADS) k_dht_row_tma(const __grid_constant__ DhtRowTmaArgs<T> a) {
   using S = TmaRowShape<T, L>;
   constexpr int R = S::R, TH = S::TH, TB = S::TILE_BYTES;
-  constexpr int NF = (MODE == kDhtUpdate) ? 4 : 1;   // fields per stage: r (, x, p, q)
+  constexpr int NF = (MODE == kDhtUpdate) ? 2 : 1;   // fields per stage: r (, q)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  // stage b: r at smem + (b NF + 0) TB, x at +1, p at +2, q at +3
+  // stage b: r at smem + (b NF + 0) TB, q at +1
   auto fld = [&](int b, int f) { return smem + (b * NF + f) * TB; };
   cpx<T>* xbuf = reinterpret_cast<cpx<T>*>(smem + 2 * NF * TB);
   cpx<T>* tws = reinterpret_cast<cpx<T>*>(smem + 2 * NF * TB + S::XBYTES);
@@ -1058,11 +1078,7 @@ __global__ void __launch_bounds__(TmaRowShape<T, L>::THREADS) k_dht_row_tma(cons
     ++issued;
     mbar_expect_tx(&full[b], NF * TB);
     tma_load2(fld(b, 0), &a.map_r, 0, row0, &full[b]);
-    if (MODE == kDhtUpdate) {
-      tma_load2(fld(b, 1), &a.map_x, 0, row0, &full[b]);
-      tma_load2(fld(b, 2), &a.map_p, 0, row0, &full[b]);
-      tma_load2(fld(b, 3), &a.map_q, 0, row0, &full[b]);
-    }
+    if (MODE == kDhtUpdate) tma_load2(fld(b, 1), &a.map_q, 0, row0, &full[b]);
   };
   if (threadIdx.x == 0) {
     mbar_init(&full[0], 1);
@@ -1092,12 +1108,7 @@ __global__ void __launch_bounds__(TmaRowShape<T, L>::THREADS) k_dht_row_tma(cons
       T* r1 = row_elem<T, L>(fld(b, 0), rb, n);
       cpx<T> rv = {*r0, *r1};
       if (MODE == kDhtUpdate) {
-        T* x0 = row_elem<T, L>(fld(b, 1), ra, n);
-        T* x1 = row_elem<T, L>(fld(b, 1), rb, n);
-        const T p0 = *row_elem<T, L>(fld(b, 2), ra, n), p1 = *row_elem<T, L>(fld(b, 2), rb, n);
-        const T q0 = *row_elem<T, L>(fld(b, 3), ra, n), q1 = *row_elem<T, L>(fld(b, 3), rb, n);
-        *x0 += alpha * p0;
-        *x1 += alpha * p1;
+        const T q0 = *row_elem<T, L>(fld(b, 1), ra, n), q1 = *row_elem<T, L>(fld(b, 1), rb, n);
         rv.x -= alpha * q0;
         rv.y -= alpha * q1;
         *r0 = rv.x;
@@ -1114,9 +1125,10 @@ __global__ void __launch_bounds__(TmaRowShape<T, L>::THREADS) k_dht_row_tma(cons
     }
     fft_ab<T, L, -1, kTwGlobal>(v, sm, t, twA);
     hartley_combine<T, L, true>(v, t);
-    // Hartley values go to the p tile (update) or back into the r tile (setup)
-    unsigned char* ob = (MODE == kDhtUpdate) ? fld(b, 2) : fld(b, 0);
-    if (MODE != kDhtUpdate) __syncwarp();
+    // Hartley values go to the q tile (update) or back into the r tile (setup);
+    // this group's q values were read before the exchange's __syncwarp
+    unsigned char* ob = (MODE == kDhtUpdate) ? fld(b, 1) : fld(b, 0);
+    __syncwarp();
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const int n = idx_b<L>(r, t);
@@ -1127,10 +1139,7 @@ __global__ void __launch_bounds__(TmaRowShape<T, L>::THREADS) k_dht_row_tma(cons
     __syncthreads();
     if (threadIdx.x == 0) {
       const int row0 = int(tile * S::ROWS);
-      if (MODE == kDhtUpdate) {
-        tma_store2(&a.map_x, fld(b, 1), 0, row0);
-        tma_store2(&a.map_r, fld(b, 0), 0, row0);
-      }
+      if (MODE == kDhtUpdate) tma_store2(&a.map_r, fld(b, 0), 0, row0);
       tma_store2(&a.map_out, ob, 0, row0);
       bulk_commit();
     }
