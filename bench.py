@@ -84,6 +84,8 @@ def measured_peaks():
     return FALLBACK_HBM_GBS, "fallback"
 
 
+FP64_RTOL = 1e-10   # PCG tolerance of the FP64 arm (the plain FP64 solve of the 64^3 workload)
+
 def csrc_hash():
     """Hash of the CUDA sources of the tumor solver (the registration and the
     allocation-free entry point are other translation units and do not
@@ -554,7 +556,7 @@ def run_ours(args, rank, world, local):
     if args.fp64_steps > 0 and rank == 0:
         del ctx
         torch.cuda.empty_cache()
-        c64 = R.context_for(prob, prec="fp64", pcg_rtol=1e-10, pcg_maxit=1000, ckpt_stride=args.ckpt_stride)
+        c64 = R.context_for(prob, prec="fp64", pcg_rtol=FP64_RTOL, pcg_maxit=1000, ckpt_stride=args.ckpt_stride)
         c64.rd_set_data(d_dev)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -600,6 +602,10 @@ def run_ours(args, rank, world, local):
                      "oracle_pcg_rtol": want["case"]["rtol"]}
         if fp64 is not None:
             vs_oracle["fp64_grad_rel_l2"] = float(np.linalg.norm(g64 - g_or) / np.linalg.norm(g_or))
+            vs_oracle["fp64_pcg_rtol"] = FP64_RTOL
+            vs_oracle["fp64_note"] = ("the FP64 arm solves to rtol 1e-10 (the tolerance of the plain FP64 solve); "
+                                      "its distance to the rtol-1e-12 oracle run is that tolerance. Solved to 1e-12 "
+                                      "the FP64 path is within 1e-10 of this oracle run (tests/test_golden_full.py)")
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
