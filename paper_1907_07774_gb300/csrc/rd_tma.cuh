@@ -242,6 +242,7 @@ __global__ void __launch_bounds__(TmaShape<T, L>::THREADS) k_op_tma(const __grid
     cpx<T> v[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = *tile_pair<T>(u_buf, idx_a<L>(r, t), g);
+    fence_proxy_async();   // the reads above come before the next copy into this buffer
     __syncthreads();   // every u value is in registers
     if (threadIdx.x == 0) {
       if (more) issue(u_buf, &a.map_u, &ubar, pu, tile_at(j + stride));
@@ -267,6 +268,7 @@ __global__ void __launch_bounds__(TmaShape<T, L>::THREADS) k_op_tma(const __grid
       v[r].y *= k.y;
     }
     red += double(loc);
+    fence_proxy_async();   // the reads above come before the next copy into this buffer
     __syncthreads();   // every kappa value is in registers
     if (threadIdx.x == 0 && more) issue(k_buf, &a.map_k, &kbar, pk, tile_at(j + stride));
     fft_ab<T, L, -1, kTwShared>(v, sm, t, twA);
@@ -367,6 +369,7 @@ __global__ void __launch_bounds__(TmaShape<T, L>::THREADS) k_op_tma_red(const __
     cpx<T> v[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = *tile_pair<T>(u_buf, idx_a<L>(r, t), g);
+    fence_proxy_async();   // the reads above come before the next copy into this buffer
     __syncthreads();   // every u value is in registers
     if (threadIdx.x == 0) {
       if (more) issue(u_buf, &a.map_u, &ubar, pu, tile_at(j + stride));
@@ -622,6 +625,7 @@ __global__ void __launch_bounds__(TmaShape<T, L>::THREADS) k_grad_tma(const __gr
       du[r] = *tile_pair<T>(a_buf, idx_a<L>(r, t), g);
       if (two) du[r] = du[r] + *tile_pair<T>(b_buf, idx_a<L>(r, t), g);
     }
+    fence_proxy_async();   // the reads above come before the next copy into this buffer
     __syncthreads();   // every u0 and u1 value is in registers
     if (threadIdx.x == 0) {
       issue(a_buf, &a.map_k, &abar, pa, tile);
@@ -637,6 +641,7 @@ __global__ void __launch_bounds__(TmaShape<T, L>::THREADS) k_grad_tma(const __gr
     cpx<T> dw[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) dw[r] = *tile_pair<T>(c_buf, idx_a<L>(r, t), g);
+    fence_proxy_async();   // the reads above come before the next copy into this buffer
     __syncthreads();   // every w value is in registers
     if (threadIdx.x == 0 && more) issue(c_buf, &a.map_w, &cbar, pc, tile_at(j + stride));
     fft_ab<T, L, -1, kTwShared>(dw, sm, t, twA);
@@ -653,6 +658,7 @@ __global__ void __launch_bounds__(TmaShape<T, L>::THREADS) k_grad_tma(const __gr
       loc += k.x * du[r].x * dw[r].x + k.y * du[r].y * dw[r].y;
     }
     red += double(loc * scale);
+    fence_proxy_async();   // the reads above come before the next copy into this buffer
     __syncthreads();   // every kappa value is in registers
     if (threadIdx.x == 0 && more) issue(a_buf, &a.map_u0, &abar, pa, tile_at(j + stride));
   }
@@ -691,7 +697,7 @@ struct TmaRowShape {
   static constexpr int XBYTES = PAIRS * XSTRIDE * int(sizeof(cpx<T>));
   static constexpr bool OK = (THREADS >= 32) && (THREADS % 32 == 0);
   static constexpr int TWBYTES = 0;   // twiddles are read from global memory (kTwGlobal)
-  static constexpr size_t OPX_SMEM = 4 * size_t(TILE_BYTES) + XBYTES + TWBYTES + 128;
+  static constexpr size_t OPX_SMEM = 2 * size_t(TILE_BYTES) + XBYTES + TWBYTES + 128;
   static constexpr size_t OPROW_SMEM = 2 * size_t(TILE_BYTES) + XBYTES + TWBYTES + 128;
   static constexpr size_t UPD_SMEM = 4 * size_t(TILE_BYTES) + XBYTES + TWBYTES + 1024;
   static constexpr size_t SETUP_SMEM = 2 * size_t(TILE_BYTES) + XBYTES + TWBYTES + 1024;
@@ -787,6 +793,7 @@ __global__ void __launch_bounds__(TmaRowShape<T, L>::THREADS) k_op_row_tma(const
       const int n = idx_a<L>(r, t);
       v[r] = {*row_elem<T, L>(u_buf, ra, n), *row_elem<T, L>(u_buf, rb, n)};
     }
+    fence_proxy_async();   // the reads above come before the next copy into this buffer
     __syncthreads();   // every u value is in registers
     if (threadIdx.x == 0 && more) issue(u_buf, &a.map_u, &ubar, pu, tile + stride);
     fft_ab<T, L, -1, kTwGlobal>(v, sm, t, twA);
@@ -802,6 +809,7 @@ __global__ void __launch_bounds__(TmaRowShape<T, L>::THREADS) k_op_row_tma(const
       v[r].x *= *row_elem<T, L>(k_buf, ra, n);
       v[r].y *= *row_elem<T, L>(k_buf, rb, n);
     }
+    fence_proxy_async();   // the reads above come before the next copy into this buffer
     __syncthreads();   // every kappa value is in registers
     if (threadIdx.x == 0 && more) issue(k_buf, &a.map_k, &kbar, pk, tile + stride);
     fft_ab<T, L, -1, kTwGlobal>(v, sm, t, twA);
@@ -846,28 +854,28 @@ struct PcgOpxTmaArgs {
 
 // z = H_2(w); p = z + beta p; q = p - s k_f d_2(kappa d_2 p)  (fields written
 // at layout-B positions of each pencil); reduces |p|^2 and sum kappa
-// (L d_2 p)^2.  The three inputs w, p and kappa have one tile buffer each;
-// the next tile of each is requested as soon as the current one is in
-// registers.  The new p and q leave from registers: in layout B the TH lanes
-// of a group hold TH consecutive elements of a row per register, so the
-// stores are coalesced.  q = p + ... takes p from a register copy when that
-// copy is small, else re-reads the value this thread has just stored.
+// (L d_2 p)^2.  Two tile buffers, each holding two fields in turn: w, then
+// the x of the deferred update (buffer 0); the old p, then kappa (buffer 1).
+// w is in registers before x is needed, and p before kappa, so every load
+// is issued as soon as its buffer is free: x while the Hartley pass runs,
+// kappa and the next w after it, the next p once kappa is in registers.
+// Two buffers instead of four leave room for more blocks per SM.  The new p
+// and q leave from registers: in layout B the TH lanes of a group hold TH
+// consecutive elements of a row per register, so the stores are coalesced.
+// q = p + ... takes p from a register copy when that copy is small, else
+// re-reads the value this thread has just stored.
 template <typename T, int L>
 __global__ void __launch_bounds__(TmaRowShape<T, L>::THREADS) k_pcg_opx_tma(const __grid_constant__ PcgOpxTmaArgs<T> a) {
   using S = TmaRowShape<T, L>;
   constexpr int R = S::R, TH = S::TH, TB = S::TILE_BYTES;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-  unsigned char* w_buf = smem;
-  unsigned char* k_buf = smem + TB;
-  unsigned char* p_buf = smem + 2 * TB;
-  unsigned char* x_buf = smem + 3 * TB;
-  cpx<T>* xbuf = reinterpret_cast<cpx<T>*>(smem + 4 * TB);
-  cpx<T>* tws = reinterpret_cast<cpx<T>*>(smem + 4 * TB + S::XBYTES);
+  unsigned char* buf0 = smem;        // w, then x
+  unsigned char* buf1 = smem + TB;   // old p, then kappa
+  cpx<T>* xbuf = reinterpret_cast<cpx<T>*>(smem + 2 * TB);
   const cpx<T>* twA = a.twA;   // read through L1 (kTwGlobal)
   const cpx<T>* twB = a.twB;
-  (void)tws;
-  __shared__ uint64_t wbar, kbar, pbar;
+  __shared__ uint64_t wbar, xbar, pbar, kbar;
   const int g = threadIdx.x / TH, t = threadIdx.x % TH;
   cpx<T>* sm = xbuf + g * S::XSTRIDE;
   const long long ntiles = a.g.nn / L / S::ROWS;
@@ -879,50 +887,36 @@ __global__ void __launch_bounds__(TmaRowShape<T, L>::THREADS) k_pcg_opx_tma(cons
   const T beta = T(betad);
   const T alpha = xupd ? T(a.st->alpha) : T(0);
   const T coef = T(-a.prm->s * a.prm->k_f / (double(L) * double(L)));
-  TmaPending pw, pk, pp;
+  TmaPending pw, px, pp, pk;
   auto issue = [&](unsigned char* dst, const CUtensorMap* map, uint64_t* bar, TmaPending& pd, long long tile) {
     mbar_expect_tx(bar, TB);
     tma_load2(dst, map, 0, int(tile * S::ROWS), bar);
     ++pd.issued;
   };
-  // old p and, with the deferred update, x of the same tile on one barrier
-  auto issue_px = [&](long long tile) {
-    mbar_expect_tx(&pbar, xupd ? 2 * TB : TB);
-    tma_load2(p_buf, &a.map_p, 0, int(tile * S::ROWS), &pbar);
-    if (xupd) tma_load2(x_buf, &a.map_x, 0, int(tile * S::ROWS), &pbar);
-    ++pp.issued;
-  };
   if (threadIdx.x == 0) {
     mbar_init(&wbar, 1);
-    mbar_init(&kbar, 1);
+    mbar_init(&xbar, 1);
     mbar_init(&pbar, 1);
+    mbar_init(&kbar, 1);
     fence_barrier_init();
   }
   __syncthreads();
   const long long t0 = blockIdx.x, stride = gridDim.x;
-  // next tile of this block's sequence, from `from` on, whose kappa is needed
-  auto next_act = [&](long long from) {
-    while (from < ntiles && a.rowact && !a.rowact[from]) from += stride;
-    return from;
-  };
   if (threadIdx.x == 0 && t0 < ntiles) {
-    issue(w_buf, &a.map_w, &wbar, pw, t0);
-    const long long kt = next_act(t0);
-    if (kt < ntiles) issue(k_buf, &a.map_k, &kbar, pk, kt);
-    if (use_p) issue_px(t0);
+    issue(buf0, &a.map_w, &wbar, pw, t0);
+    if (use_p) issue(buf1, &a.map_p, &pbar, pp, t0);
   }
   bool bad = false;
   double red_pp = 0.0, red_k = 0.0;
-  int i = 0;
   const int ra = 2 * g, rb = 2 * g + 1;
-  for (long long tile = t0; tile < ntiles; tile += stride, ++i) {
+  for (long long tile = t0; tile < ntiles; tile += stride) {
     const bool more = tile + stride < ntiles;
     const bool act = !a.rowact || a.rowact[tile] != 0;
     T* prow_a = a.p + (tile * S::ROWS + ra) * L;
     T* prow_b = a.p + (tile * S::ROWS + rb) * L;
     T* qrow_a = a.q + (tile * S::ROWS + ra) * L;
     T* qrow_b = a.q + (tile * S::ROWS + rb) * L;
-    bool ok = mbar_wait(&wbar, i & 1);
+    bool ok = mbar_wait(&wbar, pw.done & 1);
     if (__syncthreads_or(!ok)) { bad = true; break; }
     ++pw.done;
     cpx<T> v[R];
@@ -930,10 +924,13 @@ __global__ void __launch_bounds__(TmaRowShape<T, L>::THREADS) k_pcg_opx_tma(cons
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const int n = idx_a<L>(r, t);
-      v[r] = {*row_elem<T, L>(w_buf, ra, n), *row_elem<T, L>(w_buf, rb, n)};
+      v[r] = {*row_elem<T, L>(buf0, ra, n), *row_elem<T, L>(buf0, rb, n)};
     }
-    __syncthreads();   // every w value is in registers
-    if (threadIdx.x == 0 && more) issue(w_buf, &a.map_w, &wbar, pw, tile + stride);
+    // every w value is in registers: buffer 0 takes x (the proxy fence
+    // orders these shared-memory reads before the copy engine's write)
+    fence_proxy_async();
+    __syncthreads();
+    if (threadIdx.x == 0 && xupd) issue(buf0, &a.map_x, &xbar, px, tile);
     constexpr bool KEEP_P = R * int(sizeof(T)) <= 64;
     cpx<T> pv[KEEP_P ? R : 1];
     // Five transforms per tile through two copies of the transform code (a
@@ -956,24 +953,33 @@ __global__ void __launch_bounds__(TmaRowShape<T, L>::THREADS) k_pcg_opx_tma(cons
       if (step == 0) {
         hartley_combine<T, L, true>(v, t);
         if (use_p) {
-          ok = mbar_wait(&pbar, i & 1);
+          ok = mbar_wait(&pbar, pp.done & 1);
+          if (ok && xupd) ok = mbar_wait(&xbar, px.done & 1);
           if (__syncthreads_or(!ok)) { bad = true; break; }
           ++pp.done;
+          if (xupd) ++px.done;
           T* xrow_a = xupd ? a.x + (tile * S::ROWS + ra) * L : nullptr;
           T* xrow_b = xupd ? a.x + (tile * S::ROWS + rb) * L : nullptr;
 #pragma unroll
           for (int r = 0; r < R; ++r) {
             const int n = idx_b<L>(r, t);
-            const T pa = *row_elem<T, L>(p_buf, ra, n), pb = *row_elem<T, L>(p_buf, rb, n);
+            const T pa = *row_elem<T, L>(buf1, ra, n), pb = *row_elem<T, L>(buf1, rb, n);
             v[r].x += beta * pa;
             v[r].y += beta * pb;
             if (xupd) {
-              xrow_a[n] = *row_elem<T, L>(x_buf, ra, n) + alpha * pa;
-              xrow_b[n] = *row_elem<T, L>(x_buf, rb, n) + alpha * pb;
+              xrow_a[n] = *row_elem<T, L>(buf0, ra, n) + alpha * pa;
+              xrow_b[n] = *row_elem<T, L>(buf0, rb, n) + alpha * pb;
             }
           }
-          __syncthreads();   // every old p (and x) value is in registers
-          if (threadIdx.x == 0 && more) issue_px(tile + stride);
+          fence_proxy_async();
+          __syncthreads();   // every old p and x value is in registers: both buffers are free
+        }
+        if (threadIdx.x == 0) {
+          if (act)
+            issue(buf1, &a.map_k, &kbar, pk, tile);
+          else if (use_p && more)
+            issue(buf1, &a.map_p, &pbar, pp, tile + stride);
+          if (more) issue(buf0, &a.map_w, &wbar, pw, tile + stride);
         }
 #pragma unroll
         for (int r = 0; r < R; ++r) {
@@ -993,16 +999,14 @@ __global__ void __launch_bounds__(TmaRowShape<T, L>::THREADS) k_pcg_opx_tma(cons
 #pragma unroll
         for (int r = 0; r < R; ++r) {
           const int n = idx_b<L>(r, t);
-          const T ka = *row_elem<T, L>(k_buf, ra, n), kb = *row_elem<T, L>(k_buf, rb, n);
+          const T ka = *row_elem<T, L>(buf1, ra, n), kb = *row_elem<T, L>(buf1, rb, n);
           lk += ka * v[r].x * v[r].x + kb * v[r].y * v[r].y;
           v[r].x *= ka;
           v[r].y *= kb;
         }
-        __syncthreads();   // every kappa value is in registers
-        if (threadIdx.x == 0) {
-          const long long kt = next_act(tile + stride);
-          if (kt < ntiles) issue(k_buf, &a.map_k, &kbar, pk, kt);
-        }
+        fence_proxy_async();
+        __syncthreads();   // every kappa value is in registers: buffer 1 takes the next p
+        if (threadIdx.x == 0 && use_p && more) issue(buf1, &a.map_p, &pbar, pp, tile + stride);
       }
     }
     if (bad) break;
@@ -1029,8 +1033,9 @@ __global__ void __launch_bounds__(TmaRowShape<T, L>::THREADS) k_pcg_opx_tma(cons
       a.st->status = kStTimeout;
       a.st->sticky = kStTimeout;
       drain(&wbar, pw);
-      drain(&kbar, pk);
+      drain(&xbar, px);
       drain(&pbar, pp);
+      drain(&kbar, pk);
     }
     return;
   }
