@@ -422,6 +422,26 @@ def test_gradient_128_central_differences_fp64():
     assert rel(gm, g) <= 2e-4 and abs(Jm - J0) <= 2e-4 * J0
 
 
+def test_gradient_128_mixed_repeats_bit_for_bit_with_fields_in_l2():
+    """At 128^3 every FP32 field (8 MB) stays in the 129 MB L2, so a TMA
+    reload of a tile buffer completes quickly after the block's threads have
+    read the buffer; the reads are ordered before the reload by a proxy
+    fence.  Without it the direction kernel, which reuses its two buffers
+    within a tile, read a reloaded value now and then and a PCG solve did
+    not converge.  Repeated gradients must agree bit for bit, take the same
+    PCG iterations and converge."""
+    prob = synth.calibration_problem(n=128, nt=16, m=4)
+    ctx = R.context_for(prob, prec="mixed", pcg_rtol=1e-6, pcg_maxit=500)
+    ctx.rd_set_data(_calibration_data(prob, ctx))
+    J0, g0 = ctx.rd_gradient(prob.p, prob.k_f, prob.rho_f)
+    it0 = ctx.rd_last_pcg_iters()
+    assert ctx.rd_last_graph_solves() > 0
+    for _ in range(4):
+        J, g = ctx.rd_gradient(prob.p, prob.k_f, prob.rho_f)
+        assert J == J0 and np.array_equal(g, g0)
+        assert ctx.rd_last_pcg_iters() == it0
+
+
 def test_gradient_256_mixed_against_fp64_and_hessian_symmetry():
     """256^3, nt = 32, 125 Gaussians (the benchmark workload): the mixed
     gradient against the FP64 gradient of the same GPU, and symmetry of the
