@@ -68,7 +68,21 @@ def job_rate(units_per_rank, world, ms_max):
 
 def problem(n, nt):
     from paper_1907_07774_gb300 import synth
-    return synth.calibration_problem(n=n, nt=nt, m=5)
+    return synth.calibration_problem(n=n, nt=nt, m=round(GRADIENT_GAUSSIANS ** (1 / 3)))
+
+
+GRADIENT_GAUSSIANS = 125   # 5^3 Gaussians of the calibration recipe at the benchmark grid
+
+
+def gradient_config(n, nt, np_, ckpt_stride, world):
+    """The workload both arms measure: one reduced gradient (forward solve,
+    adjoint solve, gradient) of the calibration problem, PCG rtol 1e-6.  The
+    arithmetic each arm uses is in its dtype and its own keys, not here."""
+    return {"workload": f"rd_gradient {n}^3 nt={nt} np={np_} pcg_rtol=1e-6", "grid": n, "nt": nt, "np": np_,
+            "ckpt_stride": ckpt_stride,
+            "l2": f"inputs larger than L2 (fields {n ** 3 * 4 / 2 ** 20:.0f} MiB in FP32, working set "
+                  f"{n ** 3 * 4 * (nt + 18) / 2 ** 30:.1f} GiB)",
+            "parallelism": "replicas" if world > 1 else "single"}
 
 
 def measured_peaks():
@@ -404,8 +418,8 @@ def run_reference(args, rank, world):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": f"rd_gradient {n}^3 nt={nt} np=125 fp64 oracle, "
-                                                        f"per-iteration sample"},
+            "data": "synthetic", "config": gradient_config(n, nt, GRADIENT_GAUSSIANS, args.ckpt_stride, world),
+            "arithmetic": "the FP64 CPU oracle (numpy FFT), one core",
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
                              "nproc": os.cpu_count(), "cpu_model": cpu_model()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -610,11 +624,8 @@ def run_ours(args, rank, world, local):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": f"rd_gradient {n}^3 nt={nt} np={len(p)} mixed (FP32 fields, FP64 "
-                                       f"reductions) pcg_rtol=1e-6", "grid": n, "nt": nt, "np": len(p),
-                           "ckpt_stride": args.ckpt_stride, "l2": "inputs larger than L2 (fields 64 MiB, "
-                                                                 "working set > 2 GiB)",
-                           "parallelism": "replicas" if world > 1 else "single"},
+                "config": gradient_config(n, nt, len(p), args.ckpt_stride, world),
+                "arithmetic": "mixed: FP32 fields, FP64 reductions and PCG scalars",
                 "misfit": J, "pcg_iters_per_step": iters, "pcg_solves_per_step": solves,
                 "pcg_graph_solves_per_step": graph_solves,
                 "data_labels": data_src, "vs_fp64_oracle": vs_oracle,

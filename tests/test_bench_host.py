@@ -70,5 +70,19 @@ def test_reference_arm_without_stored_work_prints_unavailable(tmp_path, monkeypa
     assert line["impl"] == "reference" and "unavailable" in line
 
 
+def test_reference_arm_measures_the_same_config_as_ours(monkeypatch, capsys):
+    """Both arms time the same workload: the reference line carries the very
+    config dict of our arm (the oracle's arithmetic goes in its own keys).
+    The oracle sample is replaced by fixed times so that nothing heavy runs."""
+    import argparse
+    monkeypatch.setattr(bench, "cpu_oracle_sample", lambda n, nt, k_f: (2.5, 0.75))
+    args = argparse.Namespace(n=256, nt=32, warmup=0, steps=1, gpus=1, ckpt_stride=0)
+    assert bench.run_reference(args, 0, 1) == 0
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC and line["unit"] == bench.UNIT
+    assert line["config"] == bench.gradient_config(256, 32, bench.GRADIENT_GAUSSIANS, 0, 1)
+    assert line["e2e"]["value"] == line["value"] == line["cpu_baseline"]["value"]
+
+
 def test_cpu_model_is_a_string():
     assert isinstance(bench.cpu_model(), str) and bench.cpu_model()
