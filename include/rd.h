@@ -89,10 +89,24 @@ typedef struct {
                         (rd_set_anatomy_data); 0: tumor misfit only          */
   int coupling;      /* 1: keep the per-voxel adjoint integrands for
                         rd_coupling_field (two more fields); 0: off          */
+  int guess_restart; /* initial guesses of the state solves.  Each state solve
+                        starts from the increments of the two previous steps,
+                        extrapolated linearly in time (one previous step:
+                        that increment), with the residual formed from their
+                        stored images under (I - tau/2 A), so no operator is
+                        applied.  The extrapolation restarts from a zero
+                        guess at step 0, at every step that is a multiple of
+                        guess_restart (> 0) and, with ckpt_stride, at every
+                        segment start, so that a recomputed segment repeats
+                        the forward run bit for bit (a store-all run with
+                        guess_restart = ckpt_stride gives the same bits).
+                        -1: every state solve starts from zero.  The solves
+                        stop by the same rule either way.  Default 0.        */
 } rd_config;
 
 /* Fill *cfg with defaults: 64^3, nt 16, t_end 1, FP64, rtol 1e-10, maxit
- * 200, store all steps, k = (1, 0.1, 0), rho = (1, 0.2, 0), beta_p 0. */
+ * 200, store all steps, k = (1, 0.1, 0), rho = (1, 0.2, 0), beta_p 0,
+ * extrapolated state-solve guesses restarting only at step 0. */
 rd_status rd_config_default(rd_config* cfg);
 
 /* Device workspace in bytes that rd_create needs for cfg and np Gaussians. */

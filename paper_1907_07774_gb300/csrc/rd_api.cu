@@ -204,12 +204,19 @@ struct Carve {
 
 enum Field {
   F_KAPPA1, F_RHO1, F_C0, F_D, F_ALPHA, F_AB, F_WS, F_CN, F_CS,
-  F_X, F_R, F_P, F_Q, F_W1, F_W2, F_CH, F_CHS, F_U, F_COUNT
+  F_X, F_R, F_P, F_Q, F_W1, F_W2, F_CH, F_CHS, F_U,
+  // state-solve guesses: increments and their (I - sA) images of the last
+  // two steps (slot = step parity), and the right-hand side of the solve
+  F_GD0, F_GD1, F_GG0, F_GG1, F_FS,
+  F_COUNT
 };
 constexpr int kAnatomyFields = 6;   // m_WM, m_GM, m_CSF, m_D,WM, m_D,GM, m_D,CSF
 constexpr int kCouplingFields = 2;  // per-voxel k_f and rho_f integrands of the adjoint
 
 }  // namespace
+
+// Whether the next PCG solve starts from the guess already in x.
+__global__ void k_set_keep(PcgState* st, int keep) { st->keep_x = keep; }
 
 // Tiles of the TMA passes on which kappa1 is not identically zero.  The
 // operator d_a(kappa d_a u) and the k_f integrand kappa grad(a).grad(w)
@@ -323,6 +330,7 @@ struct Engine : EngineBase {
   cudaGraph_t pcg_graph = nullptr;
   cudaGraphExec_t pcg_exec = nullptr;
   int pcg_gen = 0;   // autotuner generation the graph was captured under
+  bool warm_next = false;   // the next pcg() starts from the guess in F_X
   bool graph_failed = false;
   int host_solves = 0;
   cudaStream_t cap_stream = nullptr;    // internal stream used only for capture
@@ -556,7 +564,8 @@ struct Engine : EngineBase {
   // ---- PCG kernels (shared by the host-driven loop and the graph) ------
   cudaError_t enqueue_setup(unsigned long long cond) {
     cudaError_t e;
-    if ((e = cudaMemsetAsync(f[F_X], 0, sizeof(T) * nn, stream)) != cudaSuccess) return e;
+    // x = 0 unless the solve starts from a guess (st->keep_x, set by pcg())
+    if ((e = L_::x_init(f[F_X], st, nn, stream)) != cudaSuccess) return e;
     DhtArgs<T> a = dht_args(2, f[F_R], f[F_W1]);
     a.fin = fin(kFinSetup);
     a.fin.cond = cond;
@@ -744,6 +753,8 @@ struct Engine : EngineBase {
   rd_status pcg() {
     cudaError_t e;
     ++last_solves;
+    k_set_keep<<<1, 1, 0, stream>>>(st, warm_next ? 1 : 0);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "pcg start");
     if (capturing) return pcg_captured();
     const bool profiling = prof_active();
     if (!profiling && !graph_failed && host_solves >= 2) {
@@ -819,6 +830,17 @@ struct Engine : EngineBase {
     return L_::normsq(a, stream);
   }
 
+  // Order of the initial guess of step n's state solve: the steps since the
+  // last restart (step 0, multiples of guess_restart, checkpoint segment
+  // starts), at most 2; -1 when guesses are off.
+  int guess_order(int n) const {
+    if (cfg.guess_restart < 0) return -1;
+    int n0 = 0;
+    if (cfg.guess_restart > 0) n0 = std::max(n0, n - n % cfg.guess_restart);
+    if (stride) n0 = std::max(n0, n - n % stride);
+    return std::min(n - n0, 2);
+  }
+
   rd_status fwd_step(int n) {
     cudaError_t e;
     rd_status rs;
@@ -832,7 +854,18 @@ struct Engine : EngineBase {
     if ((e = L_::pw(kPwFwdPre, a, stream)) != cudaSuccess) return cuda_fail(e, "fwd pre");
     if ((e = apply3(f[F_CS], f[F_R], 2.0, 1)) != cudaSuccess) return cuda_fail(e, "fwd rhs");
     if ((e = rhs_norm(f[F_CS], f[F_R], 0.5)) != cudaSuccess) return cuda_fail(e, "fwd rhs norm");
-    if ((rs = pcg()) != RD_OK) return rs;
+    const int order = guess_order(n);
+    const int s1 = (n + 1) & 1, s0 = n & 1;   // slots of steps n - 1 and n - 2 (and n)
+    if (order >= 0 && (e = L_::guess(f[F_R], f[F_X], f[F_FS], f[F_GD0 + s1], f[F_GD0 + s0], f[F_GG0 + s1],
+                                     f[F_GG0 + s0], order, nn, stream)) != cudaSuccess)
+      return cuda_fail(e, "guess");
+    warm_next = order >= 0;
+    rs = pcg();
+    warm_next = false;
+    if (rs != RD_OK) return rs;
+    if (order >= 0 &&
+        (e = L_::guess_keep(f[F_GD0 + s0], f[F_GG0 + s0], f[F_X], f[F_R], f[F_FS], nn, stream)) != cudaSuccess)
+      return cuda_fail(e, "keep guess");
     PwArgs<T> b = pw_args();
     b.a = f[F_CS];
     b.b = f[F_X];
@@ -1329,6 +1362,7 @@ struct Engine : EngineBase {
       for (int c : kClasses) set_all(c, cand);
       // a smooth right-hand side: f = A kappa1
       if ((e = apply3(f[F_KAPPA1], f[F_R], 1.0, 1)) != cudaSuccess) return cuda_fail(e, "tune rhs");
+      k_set_keep<<<1, 1, 0, stream>>>(st, 0);
       if ((e = enqueue_setup(0)) != cudaSuccess) return cuda_fail(e, "tune setup");
       if ((e = enqueue_iteration(0)) != cudaSuccess) return cuda_fail(e, "tune warm");
       rd_profile_enable(1);
@@ -1530,6 +1564,7 @@ static bool valid_config(const rd_config* c) {
   if (c->nt < 1 || !(c->t_end > 0) || !(c->pcg_rtol > 0) || c->pcg_maxit < 1) return false;
   if (c->prec != RD_FP64 && c->prec != RD_MIXED) return false;
   if (c->ckpt_stride < 0) return false;
+  if (c->guess_restart < -1) return false;
   return true;
 }
 static bool valid_shape(const rd_config* c) {
@@ -1650,6 +1685,7 @@ rd_status rd_config_default(rd_config* c) {
   c->beta_p = 0.0;
   c->moving_atlas = 0;
   c->coupling = 0;
+  c->guess_restart = 0;
   return RD_OK;
 }
 

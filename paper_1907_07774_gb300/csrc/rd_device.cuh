@@ -50,6 +50,7 @@ struct PcgState {
   int it, maxit, done, status;
   int total_it;   // iterations summed over all solves since reset
   int sticky;     // largest status seen since reset
+  int keep_x;     // 1: the solve starts from the guess already in x (set before its setup)
 };
 
 // Per-call scalars (device resident so that captured launches stay valid).

@@ -53,6 +53,10 @@ struct Launch {
                              cudaStream_t s);
   static cudaError_t normsq(const NormArgs<T>& a, cudaStream_t s);
   static cudaError_t cg_final(T* x, const T* p, const PcgState* st, long long nn, cudaStream_t s);
+  static cudaError_t x_init(T* x, const PcgState* st, long long nn, cudaStream_t s);
+  static cudaError_t guess(T* r, T* x, T* fs, const T* d1, const T* d2, const T* g1, const T* g2, int order,
+                           long long nn, cudaStream_t s);
+  static cudaError_t guess_keep(T* d, T* g, const T* x, const T* r, const T* fs, long long nn, cudaStream_t s);
 };
 
 extern template struct Launch<float>;

@@ -424,6 +424,31 @@ cudaError_t Launch<T>::cg_final(T* x, const T* p, const PcgState* st, long long 
 }
 
 template <typename T>
+cudaError_t Launch<T>::x_init(T* x, const PcgState* st, long long nn, cudaStream_t s) {
+  const void* fn = reinterpret_cast<const void*>(k_x_init<T>);
+  int grid = detail::grid_for(fn, 0, (nn + kThreads - 1) / kThreads);
+  k_x_init<T><<<grid, kThreads, 0, s>>>(x, st, nn);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Launch<T>::guess(T* r, T* x, T* fs, const T* d1, const T* d2, const T* g1, const T* g2, int order,
+                             long long nn, cudaStream_t s) {
+  const void* fn = reinterpret_cast<const void*>(k_guess<T>);
+  int grid = detail::grid_for(fn, 0, (nn + kThreads - 1) / kThreads);
+  k_guess<T><<<grid, kThreads, 0, s>>>(r, x, fs, d1, d2, g1, g2, order, nn);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Launch<T>::guess_keep(T* d, T* g, const T* x, const T* r, const T* fs, long long nn, cudaStream_t s) {
+  const void* fn = reinterpret_cast<const void*>(k_guess_keep<T>);
+  int grid = detail::grid_for(fn, 0, (nn + kThreads - 1) / kThreads);
+  k_guess_keep<T><<<grid, kThreads, 0, s>>>(d, g, x, r, fs, nn);
+  return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t Launch<T>::combine(const T* qk, const T* qr, double ca, double cb, double* out, long long nn,
                                cudaStream_t s) {
   const void* fn = reinterpret_cast<const void*>(k_combine<T>);

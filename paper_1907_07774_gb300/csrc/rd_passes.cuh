@@ -740,6 +740,52 @@ __global__ void __launch_bounds__(kThreads) k_normsq(NormArgs<T> a) {
   reduce_finish<1>(vv, a.fin);
 }
 
+// Start of a solve: x = 0, unless the solve starts from a guess already in
+// x (st->keep_x, set on the stream before the solve).
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_x_init(T* __restrict__ x, const PcgState* st, long long nn) {
+  if (st->keep_x) return;
+  for (long long i = (long long)blockIdx.x * kThreads + threadIdx.x; i < nn; i += (long long)gridDim.x * kThreads)
+    x[i] = T(0);
+}
+
+// Initial guess of a state solve (I - sA) x = f from the increments of the
+// previous one or two time steps, extrapolated in time, with its residual
+// taken from their stored images g = (I - sA) d, so that no operator is
+// applied:  order 0: x = 0, r = f;  order 1: x = d1, r = f - g1;
+// order 2: x = 2 d1 - d2, r = f - (2 g1 - g2).  f comes in r and is kept in fs.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_guess(T* __restrict__ r, T* __restrict__ x, T* __restrict__ fs,
+                                                    const T* __restrict__ d1, const T* __restrict__ d2,
+                                                    const T* __restrict__ g1, const T* __restrict__ g2, int order,
+                                                    long long nn) {
+  for (long long i = (long long)blockIdx.x * kThreads + threadIdx.x; i < nn; i += (long long)gridDim.x * kThreads) {
+    const T f = r[i];
+    fs[i] = f;
+    if (order >= 2) {
+      x[i] = T(2) * d1[i] - d2[i];
+      r[i] = f - (T(2) * g1[i] - g2[i]);
+    } else if (order == 1) {
+      x[i] = d1[i];
+      r[i] = f - g1[i];
+    } else {
+      x[i] = T(0);
+    }
+  }
+}
+
+// After a state solve: d = x and g = f - r, which is (I - sA) x up to the
+// rounding of the residual recursion.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_guess_keep(T* __restrict__ d, T* __restrict__ g,
+                                                         const T* __restrict__ x, const T* __restrict__ r,
+                                                         const T* __restrict__ fs, long long nn) {
+  for (long long i = (long long)blockIdx.x * kThreads + threadIdx.x; i < nn; i += (long long)gridDim.x * kThreads) {
+    d[i] = x[i];
+    g[i] = fs[i] - r[i];
+  }
+}
+
 // The last deferred CG update after the iteration loop: x += alpha p when
 // at least one iteration ran.
 template <typename T>

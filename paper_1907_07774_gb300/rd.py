@@ -30,7 +30,7 @@ class rd_config(ctypes.Structure):
                 ("prec", ctypes.c_int), ("pcg_rtol", ctypes.c_double), ("pcg_maxit", ctypes.c_int),
                 ("ckpt_stride", ctypes.c_int), ("k_w", ctypes.c_double * 3),
                 ("rho_w", ctypes.c_double * 3), ("beta_p", ctypes.c_double), ("moving_atlas", ctypes.c_int),
-                ("coupling", ctypes.c_int)]
+                ("coupling", ctypes.c_int), ("guess_restart", ctypes.c_int)]
 
 
 _lib = None
@@ -166,7 +166,7 @@ class Context:
 
     def __init__(self, n, nt, np_, prec="fp64", pcg_rtol=None, pcg_maxit=200, ckpt_stride=0,
                  k_w=(1.0, 0.1, 0.0), rho_w=(1.0, 0.2, 0.0), beta_p=0.0, t_end=1.0,
-                 stream=None, device=None, moving_atlas=False, coupling=False):
+                 stream=None, device=None, moving_atlas=False, coupling=False, guess_restart=0):
         import torch
         L = lib()
         cfg = rd_config()
@@ -186,6 +186,7 @@ class Context:
         cfg.beta_p = float(beta_p)
         cfg.moving_atlas = 1 if moving_atlas else 0
         cfg.coupling = 1 if coupling else 0
+        cfg.guess_restart = int(guess_restart)
         self.cfg = cfg
         self.n = n
         self.np = int(np_)

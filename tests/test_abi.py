@@ -43,7 +43,7 @@ def test_config_default_and_workspace_size(lib):
     assert list(cfg.n) == [64, 64, 64] and cfg.nt == 16 and cfg.prec == R.RD_FP64
     nb = ctypes.c_size_t()
     assert lib.rd_workspace_size(ctypes.byref(cfg), 8, ctypes.byref(nb)) == 0
-    fields = 18 + 16      # working fields + one checkpoint slot per step
+    fields = 23 + 16      # working fields + one checkpoint slot per step
     assert nb.value >= fields * 64 ** 3 * 8 and nb.value < (fields + 8) * 64 ** 3 * 8
     cfg.prec = R.RD_MIXED
     nb32 = ctypes.c_size_t()
