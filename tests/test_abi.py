@@ -70,6 +70,25 @@ def test_invalid_arguments_are_rejected(lib):
     assert lib.rd_last_pcg_iters(None) == 0
 
 
+def test_state_solve_guesses_default_on_and_range_checked(lib):
+    """rd_config.guess_restart: 0 by default (extrapolated guesses, restarted
+    only at step 0 and at checkpoint segment starts), -1 turns them off,
+    anything below -1 is an argument error; the setting does not change the
+    workspace size."""
+    cfg = R.rd_config()
+    lib.rd_config_default(ctypes.byref(cfg))
+    assert cfg.guess_restart == 0
+    sizes = []
+    for g in (0, -1, 5):
+        cfg.guess_restart = g
+        nb = ctypes.c_size_t()
+        assert lib.rd_workspace_size(ctypes.byref(cfg), 8, ctypes.byref(nb)) == 0
+        sizes.append(nb.value)
+    assert sizes[0] == sizes[1] == sizes[2]
+    cfg.guess_restart = -2
+    assert lib.rd_workspace_size(ctypes.byref(cfg), 8, ctypes.byref(ctypes.c_size_t())) == 1
+
+
 def test_registration_config_and_argument_checks(lib):
     from paper_1907_07774_gb300 import rg as G
     L = G.lib()
