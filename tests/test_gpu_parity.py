@@ -206,6 +206,30 @@ def test_checkpoint_recompute_is_bitwise_identical(prec):
     assert np.array_equal(out[1], out[3])
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_state_solve_guesses_save_iterations_not_accuracy(prec):
+    """The extrapolated guesses of the state solves (rd_config.guess_restart
+    0) against zero starts (-1) at 64^3, nt = 16: fewer PCG iterations in the
+    forward sweep, and c(1) and the gradient agree with the oracle to the
+    same tolerance either way."""
+    prob = synth.calibration_problem(n=64, nt=16, m=4)
+    M = orc.model_from_problem(prob, rtol=1e-13, maxit=2000, kind="numpy")
+    c_true, _ = M.forward(prob.p_true, prob.k_f_true, prob.rho_f_true)
+    d = synth.labels(c_true, synth.ellipsoid_mask(prob.n), prob.seed + 7)
+    J_or, g_or, c1_or, _ = M.gradient(prob.p, prob.k_f, prob.rho_f, d)
+    iters = {}
+    for gr in (-1, 0):
+        ctx = gpu_for(prob, prec, guess_restart=gr)
+        ctx.rd_set_data(d)
+        c1 = np.zeros(prob.n)
+        ctx.rd_forward(prob.p, prob.k_f, prob.rho_f, c1)
+        iters[gr] = ctx.rd_last_pcg_iters()
+        assert rel(c1, c1_or) <= TOL[prec]
+        J, g = ctx.rd_gradient(prob.p, prob.k_f, prob.rho_f)
+        assert abs(J - J_or) <= TOL[prec] * abs(J_or) and rel(g, g_or) <= TOL[prec]
+    assert iters[0] < iters[-1], iters
+
+
 def test_graph_and_host_driven_solves_are_bitwise_identical():
     """PCG solves run as CUDA graphs with a device-side loop once a context
     is warm; with launch timing on they run host-driven.  Same bits."""
